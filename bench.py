@@ -1,0 +1,412 @@
+"""Benchmark: FP64 DOF-residual updates/s of the entropy-stable tensor-product DSEM.
+
+Workload (one GPU): periodic [0,2pi]^3, 16^3 x 6 = 24576 curved tetrahedra (sine
+warp, amplitude 0.05 L), degree p = 4 (N_p* = 35 modes, N_c = 5), Taylor-Green
+vortex at Mach 0.1 with Lax-Friedrichs interface dissipation, FP64.  One "step" is
+one classical RK4 step (four evaluations of d u~/dt, every row of the hot path),
+replayed from a CUDA graph.  DOF = n_elem * N_p* * N_c; value = 4 * DOF per step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the oracle (plain numpy, test infrastructure) on the host on a
+bounded sample of the same workload.  Under torchrun each rank runs an independent
+replica (weak scaling, no collective); rank 0 prints one JSON line.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+# the oracle's CPU baseline runs single-threaded: pin every BLAS/OpenMP pool before numpy loads
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import esd_inputs as I  # noqa: E402
+
+WORKLOAD = dict(dim=3, M=16, L=2 * np.pi, p=4, state="tgv", flux="LF")
+METRIC = "FP64 DOF-residual updates/s at p=4 tets (% FP64 roofline); adjoint/forward ratio"
+UNIT = "DOF-residual updates/s"
+
+
+# ---------------------------------------------------------------------------------
+# algorithmic FP64 flop counts (formula level: add/mul/div = 1, FMA = 2)
+# ---------------------------------------------------------------------------------
+def pair_flops(D):
+    """One directional two-point flux (Section 7.2) plus its accumulation to both ends."""
+    NC = D + 2
+    log_means = 2 * 12            # s, d, f = d/s, u = f^2, 3-term Horner series (6), division, select
+    dots = 3 * (2 * D - 1)        # v^-.n, v^+.n, v^-.v^+
+    f_rho = 3                     # rho_ln * (vn^- + vn^+)/2
+    p_avg = 2
+    momentum = 5 * D              # f_rho {{v_k}} + {{p}} n_k
+    energy = 9
+    accumulate = 2 * NC
+    return log_means + dots + f_rho + p_avg + momentum + energy + accumulate
+
+
+def interface_flops(D):
+    NC = D + 2
+    flux = pair_flops(D) - 2 * NC
+    lf = 2 * (2 * D - 1) + 5 + 2 * (2 * D + 2) + 2 * D + 3 * NC   # speeds, jumps of U, damping
+    return flux + lf + NC                                          # times B J
+
+
+def transform_fmas(D, p):
+    n = p + 1
+    Np = (p + 1) * (p + 2) // 2 if D == 2 else (p + 1) * (p + 2) * (p + 3) // 6
+    S12 = (p + 1) * (p + 2) // 2
+    Nq = n ** D
+    if D == 2:
+        V = Np * n + Nq * (p + 1)
+        VT = (p + 1) * n * n + Np * n
+    else:
+        V = Np * n + S12 * n * n + Nq * (p + 1)
+        VT = (p + 1) * n ** 3 + S12 * n * n + Np * n
+    return V, VT, Nq, Np
+
+
+def residual_kernel_flops(D, p):
+    """Per element: interface flux, volume + facet-correction pairs, lift, weight-adjusted inverse."""
+    n = p + 1
+    NC = D + 2
+    V, VT, Nq, Np = transform_fmas(D, p)
+    vol_pairs = D * n ** (D - 1) * (p * (p + 1) // 2)
+    fac_pairs = 3 * n * n if D == 2 else 3 * n ** 3 + n ** 4
+    Nfn = (D + 1) * n ** (D - 1)
+    lift = (7 * Nq) if D == 2 else (2 * n ** 3 + 9 * Nq)
+    reduce4 = 0 if D == 2 else NC * n * n * (n - 1)
+    dudt = 2 * (VT + V + VT) + Nq
+    return ((vol_pairs + fac_pairs) * pair_flops(D) + Nfn * interface_flops(D)
+            + NC * (lift + dudt) + reduce4), vol_pairs + fac_pairs + Nfn
+
+
+def project_kernel_flops(D, p):
+    n = p + 1
+    NC = D + 2
+    V, VT, Nq, Np = transform_fmas(D, p)
+    Nfn = (D + 1) * n ** (D - 1)
+    R = 6 * n * n if D == 2 else 10 * n ** 3       # facet extrapolation R (face 4 in two stages)
+    entropy_vars = Nq * (4 * D + 16)          # primitive recovery, two logs, W(u), times W J
+    cons_from_w = (Nq + Nfn) * (3 * D + 14)   # U(w): log, exp, primitive fields
+    return NC * (2 * (3 * V + 2 * VT) + Nq + R) + entropy_vars + cons_from_w
+
+
+# ---------------------------------------------------------------------------------
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def build_inputs(torch, E, dev):
+    w = WORKLOAD
+    mesh, X = I.config_mesh(w["dim"], w["M"], w["L"], w["p"], True)
+    if w["M"] != 16:
+        print(f"note: reduced mesh M={w['M']} (profiling case, not a bench line)", file=sys.stderr)
+    gm = E.Mesh(w["dim"], w["p"], X, mesh.nbr_elem, mesh.nbr_face, flux=w["flux"])
+    x = gm.volume_nodes()
+    un = np.ascontiguousarray(np.transpose(I.taylor_green(x, 0.1), (0, 2, 1)))
+    u0 = gm.l2_project(torch.from_numpy(un).to(dev))
+    torch.cuda.synchronize()
+    lam = I.max_wave_speed_sampled(lambda y: I.taylor_green(y, 0.1), 3, w["L"])
+    dt = 0.1 * (w["L"] / w["M"]) / (lam * (2 * w["p"] + 1))
+    return mesh, gm, u0, dt
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [s.strip() for s in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_ours(args):
+    import torch
+    import paper_2312_07874_gb300 as E
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    mesh, gm, u0, dt = build_inputs(torch, E, dev)
+    info = gm.info
+    D, p = WORKLOAD["dim"], WORKLOAD["p"]
+    nE = info["n_elem"]
+    dof = nE * info["n_modes"] * info["n_c"]
+    stream = torch.cuda.Stream(device=dev)
+    u = u0.clone()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    # ---- warm-up (graph capture happens on the first call) ----
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            gm.rk_step(u, dt)
+    stream.synchronize()
+    gm.check()
+    # ---- timed region: K RK4 steps ----
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+        for _ in range(args.steps):
+            gm.rk_step(u, dt)
+        ev1.record(stream)
+    stream.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    clk = clocks.stop()
+    gm.check()
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = 4.0 * dof * world / (ms * 1e-3)
+
+    # ---- dominant kernel (residual) alone, on the launching stream ----
+    out = torch.empty_like(u)
+    nrep = max(3, args.steps)
+    with torch.cuda.stream(stream):
+        E.esd_launch_stage(gm.handle, 0, u, None, stream)
+        E.esd_launch_stage(gm.handle, 1, None, out, stream)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(nrep):
+            E.esd_launch_stage(gm.handle, 1, None, out, stream)
+        b.record(stream)
+        c, d = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c.record(stream)
+        for _ in range(nrep):
+            E.esd_launch_stage(gm.handle, 0, u, None, stream)
+        d.record(stream)
+    stream.synchronize()
+    res_ms = a.elapsed_time(b) / nrep
+    proj_ms = c.elapsed_time(d) / nrep
+    rflops, npairs = residual_kernel_flops(D, p)
+    achieved = rflops * nE / (res_ms * 1e-3)
+    peak = E.esd_measure_fp64_peak(stream)
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "residual_kernel_tet_p4_traffic.json")
+    if os.path.exists(tpath):
+        tj = json.load(open(tpath))
+        if tj.get("kernel_source_sha256") == _kernel_hash():
+            traffic = tj.get("dram_bytes_per_launch")
+    pflops = project_kernel_flops(D, p)
+
+    # ---- end to end through the public API: pinned H2D, RK4 step, D2H ----
+    host_in = u0.cpu().pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    ue = torch.empty_like(u)
+    with torch.cuda.stream(stream):
+        for _ in range(2):
+            ue.copy_(host_in, non_blocking=True)
+            gm.rk_step(ue, dt)
+            host_out.copy_(ue, non_blocking=True)
+    stream.synchronize()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(args.steps):
+            ue.copy_(host_in, non_blocking=True)
+            gm.rk_step(ue, dt)
+            host_out.copy_(ue, non_blocking=True)
+        e1.record(stream)
+    stream.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    nbytes = host_in.numel() * 8
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded analytic TGV state, no dataset)",
+        "config": {"workload": "tet_tgv_curved p=4: periodic [0,2pi]^3, 16^3x6 = 24576 curved tets, TGV Ma=0.1, "
+                               "LF interface flux, RK4 step (4 residual evaluations) from a CUDA graph",
+                   "n_elem": nE, "p": p, "dof": dof, "dt": dt,
+                   "l2": "inputs larger than L2: per step the kernels stream ~1.4 GB of pair tables and states",
+                   "parallelism": f"replicas x{world} (independent meshes, no collective)"},
+        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "residual_kernel<3> (interface flux, line-based flux differencing, facet "
+                               "correction, lift, weight-adjusted inverse)",
+                     "peak_source": "measured live: FP64 FMA chain (esd_measure_fp64_peak), FMA = 2 flops",
+                     "algorithmic_flops_per_elem": rflops, "kernel_ms": res_ms,
+                     "project_kernel_ms": proj_ms, "project_flops_per_elem": pflops},
+        "two_point_fluxes_per_s": 4.0 * npairs * nE * world / (ms * 1e-3),
+        "paper_flux_count_equivalent_per_s": 4.0 * info["paper_flux_count_per_elem"] * nE * world / (ms * 1e-3),
+        "adjoint_forward_ratio": None,
+        "e2e": {"value": 4.0 * dof * world / (e2e_ms * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+        "gpu_launches": 8 * args.steps,
+        "clocks": clk,
+    }
+    if rank == 0:
+        line["cpu_baseline"] = cpu_baseline(seconds=args.cpu_seconds) if args.cpu_seconds > 0 else None
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def _kernel_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("kernels.cu", "esd_internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_2312_07874_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
+# ---------------------------------------------------------------------------------
+# oracle on the host (CPU baseline and the reference arm)
+# ---------------------------------------------------------------------------------
+_ORACLE = {}
+
+
+def _oracle_setup():
+    if "D" not in _ORACLE:
+        from oracle.residual import Discretization
+        w = WORKLOAD
+        mesh, X = I.config_mesh(w["dim"], w["M"], w["L"], w["p"], True)
+        D = Discretization(w["dim"], w["p"], X, mesh.nbr_elem, mesh.nbr_face, flux=w["flux"])
+        um = np.einsum("ij,i,eic->ecj", D.V, D.ref.w, I.taylor_green(D.geo.x_vol, 0.1))
+        _ORACLE.update(D=D, um=um)
+    return _ORACLE["D"], _ORACLE["um"]
+
+
+def _oracle_sample(D, um, n_el):
+    """d u~/dt of the sampled elements by the oracle's sparse route (the paper's algorithm):
+    entropy projection of the sample and its face neighbours, then the residual."""
+    from oracle.residual import Discretization  # noqa: F401
+    el = np.arange(n_el)
+    t0 = time.perf_counter()
+    D.rhs(um, "sparse", elems=el, chunk=n_el)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(seconds=15.0, n_el=None):
+    """Time the oracle as it stands on a bounded sample of the workload's elements."""
+    D, um = _oracle_setup()
+    n_el = n_el or 16
+    t = _oracle_sample(D, um, n_el)
+    while t < 0.25 * seconds and n_el < D.E:
+        n_el = min(D.E, n_el * 2)
+        t = _oracle_sample(D, um, n_el)
+    dof = n_el * D.Np * D.Nc
+    return {"value": dof / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n_el} of {D.E} elements of the benchmark mesh, one d u~/dt each (sparse route); "
+                      f"{t:.1f} s; includes the entropy projection of the whole mesh"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    D, um = _oracle_setup()
+    n_el = 32
+    times = []
+    for _ in range(args.warmup):
+        _oracle_sample(D, um, n_el)
+    for _ in range(args.steps):
+        times.append(_oracle_sample(D, um, n_el))
+    t = float(np.mean(times))
+    dof = n_el * D.Np * D.Nc
+    value = dof / t
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded analytic TGV state, no dataset)",
+        "impl": "reference",
+        "config": {"workload": "tet_tgv_curved p=4: periodic [0,2pi]^3, 16^3x6 = 24576 curved tets, TGV Ma=0.1, "
+                               "LF interface flux (oracle: one d u~/dt of a 32-element sample per step)",
+                   "n_elem": D.E, "p": WORKLOAD["p"]},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{n_el} elements per step, sparse route"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="0 skips the CPU baseline")
+    ap.add_argument("--mesh-m", type=int, default=16, help="cells per direction (16 = the benchmark)")
+    args = ap.parse_args()
+    WORKLOAD["M"] = args.mesh_m
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,196 @@
+/*
+ * esd.h -- C ABI of a GB300 (sm_103a) FP64 library for the entropy-stable modal
+ * discontinuous spectral-element method with tensor-product summation-by-parts
+ * operators on curved triangles and tetrahedra (Montoya & Zingg, arXiv 2312.07874).
+ *
+ * Conventions used by every entry point
+ * -------------------------------------
+ * - Arithmetic is IEEE FP64 throughout.
+ * - Modal state arrays ("u", "dudt", "w_modal", cotangents) are device pointers
+ *   to double, C-contiguous with layout [n_elem][N_c][N_p*], N_c = dim + 2,
+ *   N_p* = C(p+dim, dim).  Variables are ordered (rho, rho v_1 .. rho v_dim, E)
+ *   (Eq. (euler), Section 7.1).  Modes are the normalized PKD polynomials of
+ *   Eq. (modal_basis_2d) / Eq. (modal_basis_3d) (Section 4.3), multi-indices
+ *   alpha in lexicographic order with alpha_1 slowest:
+ *     for a1 in 0..p: for a2 in 0..p-a1: [for a3 in 0..p-a1-a2:]
+ * - Device arrays must be allocated by the caller (cudaMalloc or a framework
+ *   allocator), be 8-byte aligned, and stay alive until the stream work that
+ *   uses them completes.  The library never allocates or frees memory in the
+ *   per-step calls; everything it needs is allocated by esd_mesh_create.
+ * - "stream" is a cudaStream_t passed as void*; NULL is the legacy default
+ *   stream.  All device calls are asynchronous on that stream; a returned
+ *   ESD_OK means the work was enqueued.
+ * - Errors are returned as esd_status, never thrown or trapped on the device.
+ *   esd_last_error() returns a human-readable message for the calling thread.
+ *   Argument errors (null/host pointers, bad sizes) are detected before any
+ *   launch.  A non-admissible state (rho <= 0, p <= 0 or non-finite values at a
+ *   quadrature node) sets a device flag that esd_mesh_check() reports as
+ *   ESD_ERR_STATE.
+ * - A mesh handle may be used from one host thread at a time.
+ */
+#ifndef ESD_H
+#define ESD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  ESD_OK = 0,
+  ESD_ERR_ARG = -1,         /* invalid argument (null, host pointer, misaligned, out of range) */
+  ESD_ERR_MESH = -2,        /* J <= 0, non-conforming facets, bad connectivity */
+  ESD_ERR_CUDA = -3,        /* a CUDA runtime call failed */
+  ESD_ERR_STATE = -4,       /* non-admissible state seen by a kernel (rho <= 0, p <= 0, NaN/Inf) */
+  ESD_ERR_TIMEOUT = -5,     /* a bounded device-side wait gave up */
+  ESD_ERR_NOMEM = -6,       /* device allocation failed at create time */
+  ESD_ERR_UNSUPPORTED = -7  /* degree or size outside what this build supports */
+} esd_status;
+
+enum { ESD_FLUX_EC = 0, ESD_FLUX_LF = 1 };
+
+typedef struct esd_mesh_s* esd_mesh;
+typedef struct esd_batch_s* esd_batch;
+
+/* Mesh description (all pointers are HOST pointers, read during esd_mesh_create only).
+ *
+ * map_nodes: [n_elem][N*_p][dim] physical positions of the degree-p mapping nodes
+ *   of every element (isoparametric p_g = q = p, Section 7.3).  The nodes are the
+ *   equispaced lattice of the reference simplex, first lattice index fastest:
+ *     triangle:    for j in 0..p: for i in 0..p-j:            xi = (-1+2i/p, -1+2j/p)
+ *     tetrahedron: for k: for j: for i (i+j+k <= p): xi = (-1+2i/p, -1+2j/p, -1+2k/p)
+ *   Reference simplex: triangle (-1,-1),(1,-1),(-1,1) (Eq. (reference_triangle));
+ *   tetrahedron (-1,-1,-1),(1,-1,-1),(-1,1,-1),(-1,-1,1) (Eq. (reference_tetrahedron)).
+ * nbr_elem/nbr_face: [n_elem][N_f], the element and local facet across each local facet
+ *   (facets numbered as in Eq. (tri_facets) / Eq. (tet_facets)).  Every facet must have a
+ *   neighbour (periodic meshes).  Tetrahedra must be oriented so that both sides of
+ *   a facet collapse its quadrature rule onto the same vertex (Remark 5); the facet
+ *   node correspondence (identity or reversal of the first facet coordinate) is
+ *   found from node positions, which may differ by one constant periodic shift.
+ * gamma: ratio of specific heats (Section 7.1).
+ * flux: ESD_FLUX_LF (entropy stable, Eq. (num_flux) with Eq. (wave_speed)) or
+ *   ESD_FLUX_EC (entropy conservative: no dissipative term).
+ */
+typedef struct {
+  int dim;                  /* 2 (triangles) or 3 (tetrahedra) */
+  int p;                    /* polynomial degree p = q = p_g; 1..10 (triangles), 1..6 (tetrahedra) */
+  int64_t n_elem;
+  const double* map_nodes;
+  const int32_t* nbr_elem;
+  const int8_t* nbr_face;
+  double gamma;
+  int flux;
+} esd_mesh_desc;
+
+typedef struct {
+  int dim, p, n_c, n_modes, n_vol_nodes, n_facets, n_facet_nodes;
+  int64_t n_elem;
+  int64_t vol_pairs_per_elem;          /* line-based volume pairs, dim*q(q+1)^dim/2 */
+  int64_t facet_pairs_per_elem;        /* nnz of R^T B summed over facets */
+  int64_t paper_flux_count_per_elem;   /* Eq. (num_fluxes) */
+  size_t device_bytes;                 /* device memory held by the handle */
+  int elems_per_cta_project, elems_per_cta_residual;
+} esd_info;
+
+/* Build reference tables, curved geometry (exact adjugate metrics in 2D, conservative
+ * curl form of Eq. (conservative_curl) in 3D, Nanson normals Eq. (nanson), interpolated
+ * Jacobian Eq. (jacobian_approx)), facet connectivity, and mesh-static pair
+ * coefficients; validates J > 0 (Eq. (jacobian_positive)) and Assumption 2; uploads
+ * everything and allocates the workspace.  Synchronous.  Errors: ESD_ERR_ARG,
+ * ESD_ERR_MESH, ESD_ERR_UNSUPPORTED, ESD_ERR_NOMEM, ESD_ERR_CUDA. */
+esd_status esd_mesh_create(const esd_mesh_desc* desc, esd_mesh* out);
+esd_status esd_mesh_destroy(esd_mesh mesh);
+esd_status esd_mesh_info(esd_mesh mesh, esd_info* out);
+
+/* Synchronize the stream, then report (and clear) the device admissibility flag:
+ * ESD_OK or ESD_ERR_STATE. */
+esd_status esd_mesh_check(esd_mesh mesh, void* stream);
+
+/* Physical coordinates of the volume quadrature nodes, HOST output
+ * [n_elem][N_q][dim] in the library's node order (the same order esd_l2_project
+ * expects).  Used to evaluate initial data. */
+esd_status esd_mesh_volume_nodes(esd_mesh mesh, double* x_host);
+
+/* Reference L2 projection u~ = V^T W u of nodal data given at the volume nodes
+ * (input layout [n_elem][N_c][N_q], device) -- an input-preparation helper. */
+esd_status esd_l2_project(esd_mesh mesh, const double* u_nodal, double* u_modal, void* stream);
+
+/* Entropy projection, Eq. (entropy_expansion): w~ = M~^{-1} V^T W J W(V u~) with the
+ * weight-adjusted inverse M~^{-1} = V^T W J^{-1} V of Eq. (weight_adjusted_inverse)
+ * (M = I).  u: [n_elem][N_c][N_p*] in, w_modal: same layout out (device). */
+esd_status esd_project_entropy(esd_mesh mesh, const double* u, double* w_modal, void* stream);
+
+/* Time derivative of Eq. (dudt_modal), d u~/dt = M~^{-1} V^T r, with the nodal
+ * residual r of Eq. (entropy_stable): line-based flux differencing along the
+ * collapsed-coordinate lines, facet correction Eq. (facet_correction), interface flux
+ * Eq. (interface_flux).  u, dudt: device, [n_elem][N_c][N_p*]; u and dudt must not alias. */
+esd_status esd_rhs(esd_mesh mesh, const double* u, double* dudt, void* stream);
+
+/* Vector-Jacobian product of esd_rhs with respect to u: grad = (d rhs / d u)^T cot.
+ * The paper has no counterpart (it is the adjoint of Eq. (dudt_modal)).  u, cot, grad:
+ * device [n_elem][N_c][N_p*]; grad must not alias u or cot. */
+esd_status esd_rhs_vjp(esd_mesh mesh, const double* u, const double* cot, double* grad, void* stream);
+
+/* One classical RK4 step of size dt in place on u (not in the paper, which uses DP8).
+ * stage_ckpt: NULL or device [4][n_elem][N_c][N_p*]; when given, the four stage
+ * inputs are stored there for esd_rk_step_vjp.  The launch sequence is captured in a
+ * CUDA graph per (u, dt, stage_ckpt, stream) and replayed on later calls. */
+esd_status esd_rk_step(esd_mesh mesh, double* u, double dt, double* stage_ckpt, void* stream);
+
+/* Discrete adjoint of one esd_rk_step: given the stage checkpoints written by the forward
+ * step and the cotangent of the step's output, write the cotangent of its input.
+ * cot_out, cot_in: device [n_elem][N_c][N_p*]; they may alias (in place). */
+esd_status esd_rk_step_vjp(esd_mesh mesh, const double* stage_ckpt, double dt, const double* cot_out,
+                           double* cot_in, void* stream);
+
+/* Diagnostics of Theorems 2 and 4: out (device, N_c + 2 doubles) receives
+ * sum_kappa 1^T r^(kappa,e) for each variable e (equal to sum 1^T W J V d u~/dt), then
+ * sum_kappa sum_e w^T r (the entropy rate, zero for ESD_FLUX_EC on periodic meshes), then
+ * sum |w_i r_i| as its scale. */
+esd_status esd_diagnostics(esd_mesh mesh, const double* u, double* out, void* stream);
+
+/* Batched, persistent execution of many independent meshes (not in the paper).
+ * The batch keeps references to the meshes, which must outlive it. */
+esd_status esd_batch_create(const esd_mesh* meshes, int n, esd_batch* out);
+esd_status esd_batch_destroy(esd_batch batch);
+/* u[i], dudt[i]: device state arrays of mesh i (layouts as above). */
+esd_status esd_batch_rhs(esd_batch batch, const double* const* u, double* const* dudt, void* stream);
+/* One RK4 step of every mesh; dt[i] is a HOST array of step sizes. */
+esd_status esd_batch_rk_step(esd_batch batch, double* const* u, const double* dt, void* stream);
+
+/* Measurement hook: launch one kernel of the esd_rhs pipeline alone, so that it can be
+ * timed with events on `stream`.  stage 0: the projection kernel on u (entropy projection
+ * and entropy-projected states at all nodes, written to the handle's workspace; `out`
+ * unused, may be NULL); stage 1: the residual kernel on the workspace states left by the
+ * last stage-0 launch, writing d u~/dt to `out` (device).  esd_rhs == stage 0 then 1. */
+esd_status esd_launch_stage(esd_mesh mesh, int stage, const double* u, double* out, void* stream);
+
+/* Measurement helper: sustained FP64 FMA throughput of this device, in FP64
+ * operations (1 FMA = 2) per second, measured with a register-resident FMA chain
+ * on the given stream (synchronous). */
+esd_status esd_measure_fp64_peak(double* flops_per_s, void* stream);
+
+/* Per-element sizes for a (dim, p) pair without building a mesh (n_elem = 0,
+ * device_bytes = 0, launch fields 0).  Host only. */
+esd_status esd_ref_info(int dim, int p, esd_info* out);
+
+/* Test hook: run only the host part of esd_mesh_create (no device is touched) and
+ * copy selected host tables out.  Every output is optional (NULL skips it); sizes,
+ * with the library's internal node order (volume node c1 + n*(c2 + n*c3), facet
+ * node zeta*Nqf + a + n*b, see the kernels for the pair order):
+ *   wj [n_elem][N_q] (W J), bj [n_elem][N_f*Nqf] (B J^(kappa,zeta)),
+ *   nrm [n_elem][dim][N_f*Nqf] (unit normals), vdir [n_elem][vol_pairs*dim],
+ *   fdir [n_elem][facet_pairs*dim] (pair directions), nbr [n_elem][N_f*Nqf]
+ *   (neighbour element), nbr_node (neighbour facet node), xvol [n_elem][N_q][dim]. */
+esd_status esd_debug_host_setup(const esd_mesh_desc* desc, double* wj, double* bj, double* nrm, double* vdir,
+                                double* fdir, int32_t* nbr, int32_t* nbr_node, double* xvol);
+
+const char* esd_status_string(esd_status s);
+const char* esd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ESD_H */

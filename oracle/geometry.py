@@ -13,8 +13,9 @@ Oracle (test infrastructure only).
   COLUMNS m = 1, 2, 3 of G_lm = J d xi_l / d x_m (for which G equals the
   adjugate whenever the interpolation is exact).  Mapping-node positions are
   translated by the element's first mapping node before the interpolants are
-  formed; the curl of the interpolant of c * grad x_k vanishes identically, so
-  this changes nothing but rounding.
+  formed (and before any gradient is taken); the curl of the interpolant of
+  c * grad x_k and the gradient of a constant vanish identically, so this
+  changes nothing but rounding.
 * Facet normals and J^(kappa,zeta): Eq. (nanson).
 * J used with W (mass matrix, projection): the degree-p_g interpolant of
   det(grad x) at the mapping nodes, Eq. (jacobian_approx).
@@ -109,7 +110,8 @@ class Geometry:
         pts = np.concatenate([ref.xi] + ref.xif, axis=0)
         Lm, dLm = lagrange_simplex(dim, pg, pts)
         x = np.einsum("ti,eid->etd", Lm, X)
-        A = np.einsum("tik,eim->etmk", dLm, X)          # A[e,t,m,k] = d x_m / d xi_k
+        Xl = X - X[:, :1, :]                             # element-local translation (see header)
+        A = np.einsum("tik,eim->etmk", dLm, Xl)         # A[e,t,m,k] = d x_m / d xi_k
         self.x_vol = x[:, :ref.Nq]
         self.x_fac = [x[:, ref.Nq + z * ref.Nqf: ref.Nq + (z + 1) * ref.Nqf] for z in range(ref.Nf)]
         if dim == 2:
@@ -130,7 +132,7 @@ class Geometry:
         # interpolated Jacobian determinant (degree pg) at volume nodes
         lat = lattice(dim, pg)
         _, dLl = lagrange_simplex(dim, pg, lat)
-        Al = np.einsum("tik,eim->etmk", dLl, X)
+        Al = np.einsum("tik,eim->etmk", dLl, Xl)
         detl = np.linalg.det(Al)
         Lv, _ = lagrange_simplex(dim, pg, ref.xi)
         self.J_vol = np.einsum("ti,ei->et", Lv, detl)

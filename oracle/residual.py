@@ -62,8 +62,30 @@ class Discretization:
         t = np.einsum("ij,eic->ejc", self.V, (self.ref.w[None, :] * self.geo.J_vol[elems])[..., None] * wn)
         return self.minv(t, elems)
 
-    def states(self, um):
-        """Entropy-projected conservative states at volume and facet nodes (Eq. (entropy_variables))."""
+    def states(self, um, need=None):
+        """Entropy-projected conservative states at volume and facet nodes (Eq. (entropy_variables)).
+
+        ``need`` restricts the work to a subset of elements (the others are left at a
+        harmless admissible placeholder and must not be read)."""
+        if need is not None:
+            need = np.asarray(need)
+            sub_um = um[need]
+            wt = self.project_entropy(um, need)
+            w = np.einsum("ij,ejc->eic", self.V, wt)
+            wf = [np.einsum("ji,eic->ejc", R, w) for R in self.ref.R]
+            full = lambda x: np.broadcast_to(x[:1], (self.E,) + x.shape[1:]).copy()
+            Ut = full(euler.cons_from_entropy(w, self.gamma))
+            Ut[need] = euler.cons_from_entropy(w, self.gamma)
+            Utf = []
+            for x in wf:
+                y = euler.cons_from_entropy(x, self.gamma)
+                z = full(y)
+                z[need] = y
+                Utf.append(z)
+            W = full(w)
+            W[need] = w
+            del sub_um
+            return W, Ut, Utf
         wt = self.project_entropy(um)
         w = np.einsum("ij,ejc->eic", self.V, wt)
         wf = [np.einsum("ji,eic->ejc", R, w) for R in self.ref.R]
@@ -84,8 +106,13 @@ class Discretization:
 
     def nodal_residual(self, um, route="dense", elems=None, chunk=16, return_count=False):
         """r of Eq. (entropy_stable) for the elements ``elems``: [e, Nq, Nc]."""
-        elems = np.arange(self.E) if elems is None else np.asarray(elems)
-        w, Ut, Utf = self.states(um)
+        if elems is None:
+            elems = np.arange(self.E)
+            w, Ut, Utf = self.states(um)
+        else:
+            elems = np.asarray(elems)
+            need = np.unique(np.concatenate([elems, self.geo.nbr_elem[elems].ravel()]))
+            w, Ut, Utf = self.states(um, need if len(need) < self.E else None)
         out = []
         count = 0
         for s in range(0, len(elems), chunk):

@@ -1,0 +1,667 @@
+// C ABI of the library (declared in include/esd.h): argument checking, device
+// allocation at mesh creation, launch sequencing, and CUDA-graph replay of RK4.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "esd_internal.h"
+
+using namespace esd;
+
+namespace {
+thread_local std::string g_err;
+
+esd_status fail(esd_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+esd_status cuda_fail(cudaError_t e, const char* where) {
+  return fail(ESD_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+esd_status check_dev(const void* p, const char* name) {
+  if (!is_device_ptr(p)) return fail(ESD_ERR_ARG, std::string(name) + " is not a device pointer");
+  if (reinterpret_cast<uintptr_t>(p) % 8 != 0) return fail(ESD_ERR_ARG, std::string(name) + " is not 8-byte aligned");
+  return ESD_OK;
+}
+}  // namespace
+
+struct GraphEntry {
+  double* u;
+  double dt;
+  double* ckpt;
+  cudaStream_t s;
+  cudaGraphExec_t exec;
+};
+
+struct esd_mesh_s {
+  int dim = 0, p = 0, nc = 0;
+  int64_t E = 0;
+  RefTables ref;
+  std::vector<double> xvol;
+  DevRef R{};
+  DevMesh M{};
+  LaunchCfg L{};
+  std::vector<void*> allocs;
+  size_t bytes = 0;
+  double* ws_acc = nullptr;
+  double* ws_stage = nullptr;
+  double* ws_diag = nullptr;
+  double* ws_qbar = nullptr;   // VJP: per-node cotangents [E][nq][Ntot]
+  double* ws_qext = nullptr;   // VJP: interface cotangents for the neighbour [E][nq][Nfn]
+  double* ws_adj[4] = {nullptr, nullptr, nullptr, nullptr};  // RK adjoint: cot copy, k_b, y_b, acc
+  std::vector<GraphEntry> graphs;
+
+  template <class T>
+  esd_status alloc(T** p, size_t count) {
+    void* q = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ESD_ERR_NOMEM, "cudaMalloc failed at mesh creation");
+    }
+    allocs.push_back(q);
+    bytes += count * sizeof(T);
+    *p = static_cast<T*>(q);
+    return ESD_OK;
+  }
+  template <class T>
+  esd_status upload(T** p, const std::vector<T>& h) {
+    esd_status s = alloc(p, h.size());
+    if (s != ESD_OK) return s;
+    if (!h.empty()) {
+      cudaError_t e = cudaMemcpy(*p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) return cuda_fail(e, "upload");
+    }
+    return ESD_OK;
+  }
+  ~esd_mesh_s() {
+    for (auto& g : graphs) cudaGraphExecDestroy(g.exec);
+    for (void* q : allocs) cudaFree(q);
+  }
+};
+
+extern "C" {
+
+const char* esd_status_string(esd_status s) {
+  switch (s) {
+    case ESD_OK: return "ESD_OK";
+    case ESD_ERR_ARG: return "ESD_ERR_ARG: invalid argument";
+    case ESD_ERR_MESH: return "ESD_ERR_MESH: invalid mesh";
+    case ESD_ERR_CUDA: return "ESD_ERR_CUDA: CUDA runtime error";
+    case ESD_ERR_STATE: return "ESD_ERR_STATE: non-admissible state";
+    case ESD_ERR_TIMEOUT: return "ESD_ERR_TIMEOUT: bounded device wait gave up";
+    case ESD_ERR_NOMEM: return "ESD_ERR_NOMEM: device allocation failed";
+    case ESD_ERR_UNSUPPORTED: return "ESD_ERR_UNSUPPORTED: unsupported configuration";
+  }
+  return "unknown status";
+}
+
+const char* esd_last_error(void) { return g_err.c_str(); }
+
+esd_status esd_mesh_create(const esd_mesh_desc* d, esd_mesh* out) {
+  if (!d || !out) return fail(ESD_ERR_ARG, "null descriptor or output");
+  *out = nullptr;
+  if (d->dim != 2 && d->dim != 3) return fail(ESD_ERR_ARG, "dim must be 2 or 3");
+  if (d->n_elem <= 0 || d->n_elem > (int64_t)1 << 28) return fail(ESD_ERR_ARG, "n_elem out of range");
+  if (!d->map_nodes || !d->nbr_elem || !d->nbr_face) return fail(ESD_ERR_ARG, "null mesh arrays");
+  if (!(d->gamma > 1.0) || d->gamma > 10.0) return fail(ESD_ERR_ARG, "gamma must be in (1, 10]");
+  if (d->flux != ESD_FLUX_EC && d->flux != ESD_FLUX_LF) return fail(ESD_ERR_ARG, "flux must be ESD_FLUX_EC or ESD_FLUX_LF");
+  HostMesh H;
+  std::string err;
+  esd_status st = build_host_mesh(*d, &H, &err);
+  if (st != ESD_OK) return fail(st, err);
+  esd_mesh m = new esd_mesh_s();
+  m->dim = d->dim;
+  m->p = d->p;
+  m->nc = d->dim + 2;
+  m->E = d->n_elem;
+  m->ref = H.ref;
+  m->xvol = std::move(H.xvol);
+  const RefTables& r = m->ref;
+  // reference tables
+  std::vector<double> dt;
+  auto push = [&](const std::vector<double>& v) {
+    size_t o = dt.size();
+    dt.insert(dt.end(), v.begin(), v.end());
+    return o;
+  };
+  size_t o_psi1 = push(r.psi1), o_psi2 = push(r.psi2), o_psi3 = push(r.psi3), o_l1m = push(r.l1m),
+         o_l1p = push(r.l1p), o_l2m = push(r.l2m), o_l3m = push(r.l3m), o_L2J = push(r.L2J), o_w = push(r.wvol);
+  double* dtab = nullptr;
+  int* itab = nullptr;
+  if ((st = m->upload(&dtab, dt)) != ESD_OK || (st = m->upload(&itab, r.ints)) != ESD_OK) {
+    delete m;
+    return st;
+  }
+  DevRef& R = m->R;
+  R.dim = r.dim; R.p = r.p; R.n = r.n; R.Nq = r.Nq; R.Np = r.Np; R.Nf = r.Nf; R.Nqf = r.Nqf; R.Nfn = r.Nfn;
+  R.Ntot = r.Ntot; R.T = r.T; R.Lv = r.Lv; R.S12 = r.S12; R.nvp = r.nvp; R.nfp = r.nfp;
+  for (int i = 0; i < 4; ++i) { R.fph_off[i] = r.fph_off[i]; R.fph_len[i] = r.fph_len[i]; }
+  R.psi1 = dtab + o_psi1; R.psi2 = dtab + o_psi2; R.psi3 = dtab + o_psi3;
+  R.l1m = dtab + o_l1m; R.l1p = dtab + o_l1p; R.l2m = dtab + o_l2m; R.l3m = dtab + o_l3m; R.L2J = dtab + o_L2J;
+  R.wvol = dtab + o_w;
+  R.off1 = itab + r.i_off1; R.s12a1 = itab + r.i_s12a1; R.moff = itab + r.i_moff; R.mode = itab + r.i_mode;
+  // per-element data
+  DevMesh& M = m->M;
+  M.E = m->E;
+  M.gamma = d->gamma;
+  M.lf = d->flux == ESD_FLUX_LF;
+  double *vdir, *fdir, *wj, *wdj, *bj, *nrm;
+  int32_t *ne, *nf;
+  if ((st = m->upload(&vdir, H.vdir)) || (st = m->upload(&fdir, H.fdir)) || (st = m->upload(&wj, H.wj)) ||
+      (st = m->upload(&wdj, H.wdj)) || (st = m->upload(&bj, H.bj)) || (st = m->upload(&nrm, H.nrm)) ||
+      (st = m->upload(&ne, H.nbr_e)) || (st = m->upload(&nf, H.nbr_f))) {
+    delete m;
+    return st;
+  }
+  M.vdir = vdir; M.fdir = fdir; M.wj = wj; M.wdj = wdj; M.bj = bj; M.nrm = nrm; M.nbr_e = ne; M.nbr_f = nf;
+  const size_t nstate = (size_t)m->E * nfields(r.dim) * r.Ntot;
+  const size_t nmodal = (size_t)m->E * m->nc * r.Np;
+  if ((st = m->alloc(&M.states, nstate)) || (st = m->alloc(&M.cfac, (size_t)m->E * r.Nfn)) ||
+      (st = m->alloc(&M.flag, 1)) || (st = m->alloc(&m->ws_acc, nmodal)) || (st = m->alloc(&m->ws_stage, nmodal)) ||
+      (st = m->alloc(&m->ws_diag, (size_t)m->E * (m->nc + 2))) ||
+      (st = m->alloc(&m->ws_qbar, (size_t)m->E * m->nc * r.Ntot)) ||
+      (st = m->alloc(&m->ws_qext, (size_t)m->E * m->nc * r.Nfn)) || (st = m->alloc(&m->ws_adj[0], nmodal)) ||
+      (st = m->alloc(&m->ws_adj[1], nmodal)) || (st = m->alloc(&m->ws_adj[2], nmodal)) ||
+      (st = m->alloc(&m->ws_adj[3], nmodal))) {
+    delete m;
+    return st;
+  }
+  cudaMemset(M.flag, 0, sizeof(int));
+  m->L = choose_launch(r);
+  cudaError_t e = set_smem_limits(m->L, r.dim);
+  if (e != cudaSuccess) {
+    delete m;
+    return cuda_fail(e, "cudaFuncSetAttribute");
+  }
+  e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    delete m;
+    return cuda_fail(e, "mesh upload");
+  }
+  *out = m;
+  return ESD_OK;
+}
+
+esd_status esd_mesh_destroy(esd_mesh m) {
+  if (!m) return fail(ESD_ERR_ARG, "null mesh");
+  cudaDeviceSynchronize();
+  delete m;
+  return ESD_OK;
+}
+
+esd_status esd_mesh_info(esd_mesh m, esd_info* o) {
+  if (!m || !o) return fail(ESD_ERR_ARG, "null argument");
+  const RefTables& r = m->ref;
+  o->dim = r.dim; o->p = r.p; o->n_c = m->nc; o->n_modes = r.Np; o->n_vol_nodes = r.Nq;
+  o->n_facets = r.Nf; o->n_facet_nodes = r.Nqf; o->n_elem = m->E;
+  o->vol_pairs_per_elem = r.nvp;
+  o->facet_pairs_per_elem = r.nfp;
+  const int64_t q = r.p, n = q + 1;
+  o->paper_flux_count_per_elem = r.dim == 2 ? (q * n * n) / 2 + q * n * n + 3 * n * n
+                                            : 3 * q * n * n * n + 3 * n * n * n + n * n * n * n;
+  o->device_bytes = m->bytes;
+  o->elems_per_cta_project = m->L.ea;
+  o->elems_per_cta_residual = m->L.eb;
+  return ESD_OK;
+}
+
+esd_status esd_mesh_check(esd_mesh m, void* stream) {
+  if (!m) return fail(ESD_ERR_ARG, "null mesh");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+  int flag = 0;
+  e = cudaMemcpy(&flag, m->M.flag, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "flag read");
+  if (flag) {
+    cudaMemset(m->M.flag, 0, sizeof(int));
+    return fail(ESD_ERR_STATE, "non-admissible state (rho <= 0, p <= 0 or non-finite) at a quadrature node");
+  }
+  return ESD_OK;
+}
+
+esd_status esd_mesh_volume_nodes(esd_mesh m, double* x) {
+  if (!m || !x) return fail(ESD_ERR_ARG, "null argument");
+  std::memcpy(x, m->xvol.data(), m->xvol.size() * sizeof(double));
+  return ESD_OK;
+}
+
+esd_status esd_l2_project(esd_mesh m, const double* un, double* um, void* stream) {
+  if (!m) return fail(ESD_ERR_ARG, "null mesh");
+  esd_status st;
+  if ((st = check_dev(un, "u_nodal")) || (st = check_dev(um, "u_modal"))) return st;
+  cudaError_t e = launch_l2_project(m->R, m->M, un, um, (cudaStream_t)stream);
+  return e ? cuda_fail(e, "l2_project launch") : ESD_OK;
+}
+
+esd_status esd_project_entropy(esd_mesh m, const double* u, double* w, void* stream) {
+  if (!m) return fail(ESD_ERR_ARG, "null mesh");
+  esd_status st;
+  if ((st = check_dev(u, "u")) || (st = check_dev(w, "w_modal"))) return st;
+  cudaError_t e = launch_project(m->R, m->M, m->L, u, w, (cudaStream_t)stream);
+  return e ? cuda_fail(e, "project launch") : ESD_OK;
+}
+
+esd_status esd_rhs(esd_mesh m, const double* u, double* dudt, void* stream) {
+  if (!m) return fail(ESD_ERR_ARG, "null mesh");
+  esd_status st;
+  if ((st = check_dev(u, "u")) || (st = check_dev(dudt, "dudt"))) return st;
+  if (u == dudt) return fail(ESD_ERR_ARG, "u and dudt must not alias");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = launch_project(m->R, m->M, m->L, u, nullptr, s);
+  if (e) return cuda_fail(e, "project launch");
+  Epilogue ep{};
+  ep.mode = 0;
+  ep.dudt = dudt;
+  e = launch_residual(m->R, m->M, m->L, ep, s);
+  return e ? cuda_fail(e, "residual launch") : ESD_OK;
+}
+
+static cudaError_t rk_sequence(esd_mesh m, double* u, double dt, double* ck, cudaStream_t s) {
+  const size_t nmodal = (size_t)m->E * m->nc * m->ref.Np;
+  cudaError_t e;
+  if (ck && (e = launch_copy(u, ck, (int64_t)nmodal, s))) return e;
+  const double a[4] = {0.5, 0.5, 1.0, 0.0};
+  const double b[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+  const double* in = u;
+  for (int st = 0; st < 4; ++st) {
+    if ((e = launch_project(m->R, m->M, m->L, in, nullptr, s))) return e;
+    Epilogue ep{};
+    ep.mode = 1;
+    ep.u0 = u;
+    ep.acc_in = st == 0 ? u : m->ws_acc;
+    ep.acc_out = st == 3 ? u : m->ws_acc;
+    ep.stage_out = st == 3 ? nullptr : (ck ? ck + (size_t)(st + 1) * nmodal : m->ws_stage);
+    ep.ca = a[st] * dt;
+    ep.cb = b[st] * dt;
+    if ((e = launch_residual(m->R, m->M, m->L, ep, s))) return e;
+    in = ep.stage_out;
+  }
+  return cudaSuccess;
+}
+
+esd_status esd_rk_step(esd_mesh m, double* u, double dt, double* ck, void* stream) {
+  if (!m) return fail(ESD_ERR_ARG, "null mesh");
+  esd_status st;
+  if ((st = check_dev(u, "u"))) return st;
+  if (ck && (st = check_dev(ck, "stage_ckpt"))) return st;
+  if (!(dt == dt) || dt <= 0.0) return fail(ESD_ERR_ARG, "dt must be positive");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (s == nullptr) {  // the legacy stream cannot be captured: launch directly
+    cudaError_t e = rk_sequence(m, u, dt, ck, s);
+    return e ? cuda_fail(e, "rk launch") : ESD_OK;
+  }
+  for (auto& g : m->graphs)
+    if (g.u == u && g.dt == dt && g.ckpt == ck && g.s == s) {
+      cudaError_t e = cudaGraphLaunch(g.exec, s);
+      return e ? cuda_fail(e, "graph launch") : ESD_OK;
+    }
+  cudaGraph_t graph;
+  cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+  if (e) return cuda_fail(e, "begin capture");
+  cudaError_t e1 = rk_sequence(m, u, dt, ck, s);
+  e = cudaStreamEndCapture(s, &graph);
+  if (e1) return cuda_fail(e1, "rk capture");
+  if (e) return cuda_fail(e, "end capture");
+  cudaGraphExec_t exec;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e) return cuda_fail(e, "graph instantiate");
+  if (m->graphs.size() >= 16) {
+    cudaGraphExecDestroy(m->graphs.front().exec);
+    m->graphs.erase(m->graphs.begin());
+  }
+  m->graphs.push_back({u, dt, ck, s, exec});
+  e = cudaGraphLaunch(exec, s);
+  return e ? cuda_fail(e, "graph launch") : ESD_OK;
+}
+
+esd_status esd_diagnostics(esd_mesh m, const double* u, double* out, void* stream) {
+  if (!m) return fail(ESD_ERR_ARG, "null mesh");
+  esd_status st;
+  if ((st = check_dev(u, "u")) || (st = check_dev(out, "out"))) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = launch_project(m->R, m->M, m->L, u, nullptr, s);
+  if (e) return cuda_fail(e, "project launch");
+  Epilogue ep{};
+  ep.mode = 2;
+  ep.diag = m->ws_diag;
+  if ((e = launch_residual(m->R, m->M, m->L, ep, s))) return cuda_fail(e, "residual launch");
+  e = launch_reduce_diag(m->ws_diag, m->E, m->nc + 2, out, s);
+  return e ? cuda_fail(e, "reduce launch") : ESD_OK;
+}
+
+esd_status esd_rhs_vjp(esd_mesh m, const double* u, const double* cot, double* grad, void* stream) {
+  if (!m) return fail(ESD_ERR_ARG, "null mesh");
+  esd_status st;
+  if ((st = check_dev(u, "u")) || (st = check_dev(cot, "cot")) || (st = check_dev(grad, "grad"))) return st;
+  if (grad == u || grad == cot) return fail(ESD_ERR_ARG, "grad must not alias u or cot");
+  cudaError_t e = launch_vjp(m->R, m->M, m->L, u, cot, grad, m->ws_qbar, m->ws_qext, (cudaStream_t)stream);
+  return e ? cuda_fail(e, "vjp launch") : ESD_OK;
+}
+
+// Discrete adjoint of the RK4 step.  With stage inputs Y1..Y4 and k_s = F(Y_s):
+//   u+ = u + dt/6 (k1 + 2k2 + 2k3 + k4),  Y2 = u + dt/2 k1,  Y3 = u + dt/2 k2,  Y4 = u + dt k3.
+// Reverse: k4_b = dt/6 c;  Y4_b = J(Y4)^T k4_b;  k3_b = dt/3 c + dt Y4_b;  Y3_b = J(Y3)^T k3_b;
+//          k2_b = dt/3 c + dt/2 Y3_b;  Y2_b = J(Y2)^T k2_b;  k1_b = dt/6 c + dt/2 Y2_b;
+//          Y1_b = J(Y1)^T k1_b;  u_b = c + Y1_b + Y2_b + Y3_b + Y4_b.
+esd_status esd_rk_step_vjp(esd_mesh m, const double* ck, double dt, const double* co, double* ci, void* stream) {
+  if (!m) return fail(ESD_ERR_ARG, "null mesh");
+  esd_status st;
+  if ((st = check_dev(ck, "stage_ckpt")) || (st = check_dev(co, "cot_out")) || (st = check_dev(ci, "cot_in")))
+    return st;
+  if (!(dt == dt) || dt <= 0.0) return fail(ESD_ERR_ARG, "dt must be positive");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t nmodal = m->E * m->nc * m->ref.Np;
+  double *c = m->ws_adj[0], *kb = m->ws_adj[1], *yb = m->ws_adj[2], *acc = m->ws_adj[3];
+  const double ck_a[4] = {dt / 6.0, dt / 3.0, dt / 3.0, dt / 6.0};   // weight of c in k_s_b
+  const double ck_b[4] = {0.0, dt, 0.5 * dt, 0.5 * dt};              // weight of the previous Y_b
+  cudaError_t e;
+  if ((e = launch_copy(co, c, nmodal, s)) || (e = launch_copy(co, acc, nmodal, s))) return cuda_fail(e, "rk vjp");
+  for (int j = 0; j < 4; ++j) {
+    const int stage = 3 - j;  // Y4, Y3, Y2, Y1
+    if ((e = launch_axpby(kb, ck_a[j], c, ck_b[j], j ? yb : nullptr, nmodal, s))) return cuda_fail(e, "rk vjp");
+    if ((e = launch_vjp(m->R, m->M, m->L, ck + (size_t)stage * nmodal, kb, yb, m->ws_qbar, m->ws_qext, s)))
+      return cuda_fail(e, "rk vjp");
+    if ((e = launch_axpby(j == 3 ? ci : acc, 1.0, acc, 1.0, yb, nmodal, s))) return cuda_fail(e, "rk vjp");
+  }
+  return ESD_OK;
+}
+
+struct BatchGroup {
+  int dim = 0;
+  std::vector<int> members;          // indices into the batch's mesh list
+  std::vector<BatchItem> pitems, ritems;
+  BatchItem* d_pitems = nullptr;
+  BatchItem* d_ritems = nullptr;
+  int pthreads = 256, rthreads = 64;
+  size_t psmem = 0, rsmem = 0;
+  int pgrid = 1, rgrid = 1;
+};
+
+struct BatchGraph {
+  std::vector<const double*> u;
+  std::vector<double> dt;
+  cudaStream_t s;
+  int kind;   // 0: rhs, 1: rk step
+  std::vector<BatchMesh*> d_tables;   // device BatchMesh arrays used by the graph (one per launch)
+  cudaGraphExec_t exec;
+};
+
+struct esd_batch_s {
+  std::vector<esd_mesh> meshes;
+  std::vector<BatchGroup> groups;
+  std::vector<BatchGraph> graphs;
+  std::vector<void*> allocs;
+  ~esd_batch_s() {
+    for (auto& g : graphs) cudaGraphExecDestroy(g.exec);
+    for (void* p : allocs) cudaFree(p);
+  }
+};
+
+static int sm_count() {
+  int dev = 0, n = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n > 0 ? n : 1;
+}
+
+esd_status esd_batch_create(const esd_mesh* meshes, int n, esd_batch* out) {
+  if (!meshes || n <= 0 || !out) return fail(ESD_ERR_ARG, "invalid batch arguments");
+  for (int i = 0; i < n; ++i)
+    if (!meshes[i]) return fail(ESD_ERR_ARG, "null mesh in batch");
+  esd_batch b = new esd_batch_s();
+  b->meshes.assign(meshes, meshes + n);
+  const int sms = sm_count();
+  for (int dim = 2; dim <= 3; ++dim) {
+    BatchGroup g;
+    g.dim = dim;
+    for (int i = 0; i < n; ++i) {
+      if (meshes[i]->dim != dim) continue;
+      esd_mesh m = meshes[i];
+      const int mi = (int)g.members.size();
+      g.members.push_back(i);
+      for (int64_t e0 = 0; e0 < m->E; e0 += m->L.ea)
+        g.pitems.push_back({mi, (int)std::min<int64_t>(m->L.ea, m->E - e0), e0});
+      for (int64_t e0 = 0; e0 < m->E; e0 += m->L.eb)
+        g.ritems.push_back({mi, (int)std::min<int64_t>(m->L.eb, m->E - e0), e0});
+      g.psmem = std::max(g.psmem, m->L.sa);
+      g.rsmem = std::max(g.rsmem, m->L.sb);
+      g.pthreads = std::max(g.pthreads, m->L.ta);
+      g.rthreads = std::max(g.rthreads, m->L.tb);
+    }
+    if (g.members.empty()) continue;
+    // largest items first so that the persistent grid finishes evenly
+    auto by_cost = [&](const BatchItem& x, const BatchItem& y) {
+      const esd_mesh mx = meshes[g.members[x.mesh]], my = meshes[g.members[y.mesh]];
+      return (double)x.E * mx->ref.Nq * mx->ref.n > (double)y.E * my->ref.Nq * my->ref.n;
+    };
+    std::stable_sort(g.pitems.begin(), g.pitems.end(), by_cost);
+    std::stable_sort(g.ritems.begin(), g.ritems.end(), by_cost);
+    const int per_sm_p = std::max(1, (int)(227 * 1024 / std::max<size_t>(g.psmem, 1)));
+    const int per_sm_r = std::max(1, (int)(227 * 1024 / std::max<size_t>(g.rsmem, 1)));
+    g.pgrid = std::min<int>((int)g.pitems.size(), sms * std::min(per_sm_p, 2048 / g.pthreads));
+    g.rgrid = std::min<int>((int)g.ritems.size(), sms * std::min(per_sm_r, 2048 / g.rthreads));
+    for (auto* items : {&g.pitems, &g.ritems}) {
+      void* p = nullptr;
+      if (cudaMalloc(&p, items->size() * sizeof(BatchItem)) != cudaSuccess) {
+        delete b;
+        return fail(ESD_ERR_NOMEM, "batch item list");
+      }
+      b->allocs.push_back(p);
+      cudaMemcpy(p, items->data(), items->size() * sizeof(BatchItem), cudaMemcpyHostToDevice);
+      (items == &g.pitems ? g.d_pitems : g.d_ritems) = static_cast<BatchItem*>(p);
+    }
+    b->groups.push_back(g);
+  }
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e) {
+    delete b;
+    return cuda_fail(e, "batch create");
+  }
+  *out = b;
+  return ESD_OK;
+}
+
+esd_status esd_batch_destroy(esd_batch b) {
+  if (!b) return fail(ESD_ERR_ARG, "null batch");
+  cudaDeviceSynchronize();
+  delete b;
+  return ESD_OK;
+}
+
+// Enqueue (or capture) the batched launches.  kind 0: one d u~/dt per mesh; kind 1: one RK4 step.
+static cudaError_t batch_sequence(esd_batch b, BatchGraph& G, cudaStream_t s) {
+  const int nst = G.kind == 0 ? 1 : 4;
+  const double ra[4] = {0.5, 0.5, 1.0, 0.0};
+  const double rb[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+  cudaError_t e;
+  for (int st = 0; st < nst; ++st) {
+    for (auto& g : b->groups) {
+      std::vector<BatchMesh> tab(g.members.size());
+      for (size_t k = 0; k < g.members.size(); ++k) {
+        const int i = g.members[k];
+        esd_mesh m = b->meshes[i];
+        BatchMesh& t = tab[k];
+        t.R = m->R;
+        t.M = m->M;
+        double* u = const_cast<double*>(G.u[i]);
+        if (G.kind == 0) {
+          t.u = u;
+          t.ep = Epilogue{};
+          t.ep.mode = 0;
+          t.ep.dudt = const_cast<double*>(G.u[b->meshes.size() + i]);
+        } else {
+          const double dt = G.dt[i];
+          t.u = st == 0 ? u : m->ws_stage;
+          t.ep = Epilogue{};
+          t.ep.mode = 1;
+          t.ep.u0 = u;
+          t.ep.acc_in = st == 0 ? u : m->ws_acc;
+          t.ep.acc_out = st == 3 ? u : m->ws_acc;
+          t.ep.stage_out = st == 3 ? nullptr : m->ws_stage;
+          t.ep.ca = ra[st] * dt;
+          t.ep.cb = rb[st] * dt;
+        }
+      }
+      void* p = nullptr;
+      if ((e = cudaMalloc(&p, tab.size() * sizeof(BatchMesh)))) return e;
+      G.d_tables.push_back(static_cast<BatchMesh*>(p));
+      if ((e = cudaMemcpy(p, tab.data(), tab.size() * sizeof(BatchMesh), cudaMemcpyHostToDevice))) return e;
+    }
+  }
+  return cudaSuccess;
+}
+
+static esd_status batch_run(esd_batch b, int kind, const std::vector<const double*>& ptrs, const std::vector<double>& dts,
+                            cudaStream_t s) {
+  for (auto& G : b->graphs)
+    if (G.kind == kind && G.u == ptrs && G.dt == dts && G.s == s) {
+      cudaError_t e = cudaGraphLaunch(G.exec, s);
+      return e ? cuda_fail(e, "batch graph launch") : ESD_OK;
+    }
+  BatchGraph G;
+  G.u = ptrs;
+  G.dt = dts;
+  G.s = s;
+  G.kind = kind;
+  cudaError_t e = batch_sequence(b, G, s);  // per-launch device tables (allocated outside capture)
+  if (e) return cuda_fail(e, "batch tables");
+  for (auto* p : G.d_tables) b->allocs.push_back(p);
+  cudaStream_t cs = s;
+  cudaStream_t own = nullptr;
+  if (cs == nullptr) {  // the legacy stream cannot be captured: capture on a private stream
+    cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking);
+    cs = own;
+  }
+  cudaGraph_t graph;
+  if ((e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal))) return cuda_fail(e, "batch capture");
+  const int nst = kind == 0 ? 1 : 4;
+  size_t tix = 0;
+  cudaError_t e1 = cudaSuccess;
+  for (int st = 0; st < nst && !e1; ++st)
+    for (auto& g : b->groups) {
+      BatchMesh* tab = G.d_tables[tix++];
+      if ((e1 = launch_batch(g.dim, 0, tab, g.d_pitems, (int)g.pitems.size(), g.pgrid, g.pthreads, g.psmem, cs)))
+        break;
+      if ((e1 = launch_batch(g.dim, 1, tab, g.d_ritems, (int)g.ritems.size(), g.rgrid, g.rthreads, g.rsmem, cs)))
+        break;
+    }
+  e = cudaStreamEndCapture(cs, &graph);
+  if (e1) return cuda_fail(e1, "batch launch");
+  if (e) return cuda_fail(e, "batch end capture");
+  e = cudaGraphInstantiate(&G.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (own) cudaStreamDestroy(own);
+  if (e) return cuda_fail(e, "batch graph instantiate");
+  b->graphs.push_back(G);
+  e = cudaGraphLaunch(G.exec, s);
+  return e ? cuda_fail(e, "batch graph launch") : ESD_OK;
+}
+
+esd_status esd_batch_rhs(esd_batch b, const double* const* u, double* const* dudt, void* stream) {
+  if (!b || !u || !dudt) return fail(ESD_ERR_ARG, "null argument");
+  const size_t n = b->meshes.size();
+  std::vector<const double*> ptrs(2 * n);
+  esd_status st;
+  for (size_t i = 0; i < n; ++i) {
+    if ((st = check_dev(u[i], "u[i]")) || (st = check_dev(dudt[i], "dudt[i]"))) return st;
+    if (u[i] == dudt[i]) return fail(ESD_ERR_ARG, "u[i] and dudt[i] must not alias");
+    ptrs[i] = u[i];
+    ptrs[n + i] = dudt[i];
+  }
+  return batch_run(b, 0, ptrs, {}, (cudaStream_t)stream);
+}
+
+esd_status esd_batch_rk_step(esd_batch b, double* const* u, const double* dt, void* stream) {
+  if (!b || !u || !dt) return fail(ESD_ERR_ARG, "null argument");
+  const size_t n = b->meshes.size();
+  std::vector<const double*> ptrs(n);
+  std::vector<double> dts(n);
+  esd_status st;
+  for (size_t i = 0; i < n; ++i) {
+    if ((st = check_dev(u[i], "u[i]"))) return st;
+    if (!(dt[i] > 0.0)) return fail(ESD_ERR_ARG, "dt[i] must be positive");
+    ptrs[i] = u[i];
+    dts[i] = dt[i];
+  }
+  return batch_run(b, 1, ptrs, dts, (cudaStream_t)stream);
+}
+
+esd_status esd_launch_stage(esd_mesh m, int stage, const double* u, double* out, void* stream) {
+  if (!m) return fail(ESD_ERR_ARG, "null mesh");
+  cudaStream_t s = (cudaStream_t)stream;
+  esd_status st;
+  if (stage == 0) {
+    if ((st = check_dev(u, "u"))) return st;
+    cudaError_t e = launch_project(m->R, m->M, m->L, u, nullptr, s);
+    return e ? cuda_fail(e, "project launch") : ESD_OK;
+  }
+  if (stage == 1) {
+    if ((st = check_dev(out, "out"))) return st;
+    Epilogue ep{};
+    ep.mode = 0;
+    ep.dudt = out;
+    cudaError_t e = launch_residual(m->R, m->M, m->L, ep, s);
+    return e ? cuda_fail(e, "residual launch") : ESD_OK;
+  }
+  return fail(ESD_ERR_ARG, "stage must be 0 or 1");
+}
+
+esd_status esd_ref_info(int dim, int p, esd_info* o) {
+  if (!o) return fail(ESD_ERR_ARG, "null output");
+  RefTables r;
+  std::string err;
+  esd_status st = build_ref(dim, p, &r, &err);
+  if (st != ESD_OK) return fail(st, err);
+  std::memset(o, 0, sizeof(*o));
+  o->dim = r.dim; o->p = r.p; o->n_c = dim + 2; o->n_modes = r.Np; o->n_vol_nodes = r.Nq;
+  o->n_facets = r.Nf; o->n_facet_nodes = r.Nqf;
+  o->vol_pairs_per_elem = r.nvp;
+  o->facet_pairs_per_elem = r.nfp;
+  const int64_t q = r.p, n = q + 1;
+  o->paper_flux_count_per_elem = r.dim == 2 ? (q * n * n) / 2 + q * n * n + 3 * n * n
+                                            : 3 * q * n * n * n + 3 * n * n * n + n * n * n * n;
+  return ESD_OK;
+}
+
+esd_status esd_debug_host_setup(const esd_mesh_desc* d, double* wj, double* bj, double* nrm, double* vdir,
+                                double* fdir, int32_t* nbr, int32_t* nbr_node, double* xvol) {
+  if (!d) return fail(ESD_ERR_ARG, "null descriptor");
+  if (d->n_elem <= 0 || !d->map_nodes || !d->nbr_elem || !d->nbr_face) return fail(ESD_ERR_ARG, "bad mesh arrays");
+  HostMesh H;
+  std::string err;
+  esd_status st = build_host_mesh(*d, &H, &err);
+  if (st != ESD_OK) return fail(st, err);
+  auto cp = [](auto* dst, const auto& v) {
+    if (dst) std::memcpy(dst, v.data(), v.size() * sizeof(v[0]));
+  };
+  cp(wj, H.wj); cp(bj, H.bj); cp(nrm, H.nrm); cp(vdir, H.vdir); cp(fdir, H.fdir);
+  cp(nbr, H.nbr_e); cp(nbr_node, H.nbr_f); cp(xvol, H.xvol);
+  return ESD_OK;
+}
+
+esd_status esd_measure_fp64_peak(double* flops, void* stream) {
+  if (!flops) return fail(ESD_ERR_ARG, "null output");
+  cudaError_t e = measure_fp64(flops, (cudaStream_t)stream);
+  return e ? cuda_fail(e, "fp64 probe") : ESD_OK;
+}
+
+}  // extern "C"

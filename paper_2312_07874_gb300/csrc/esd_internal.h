@@ -1,0 +1,137 @@
+// Internal declarations shared by the host setup (setup.cpp), the kernels
+// (kernels.cu) and the C ABI (api.cu).  Not part of the public interface.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "esd.h"
+
+namespace esd {
+
+constexpr int kMaxPTri = 10;
+constexpr int kMaxPTet = 6;
+
+// Number of per-node fields kept for the two-point flux: rho, v_1..v_d, p,
+// beta = rho/p, ln rho, ln beta.
+constexpr int nfields(int dim) { return dim + 5; }
+
+// Reference-element tables for one (dim, p), built on the host (setup.cpp).
+// Index conventions (internal to the library):
+//   volume node   v = c1 + n*(c2 + n*c3)          (c_k = index along eta_k)
+//   facet node    f = zeta*Nqf + j, j = a + n*b    (a along the first facet
+//                 coordinate, b along the second; triangles j = a)
+//   modes         the ABI order (alpha_1 slowest)
+struct RefTables {
+  int dim = 0, p = 0, n = 0, Nq = 0, Np = 0, Nf = 0, Nqf = 0, Nfn = 0, Ntot = 0;
+  int T = 0;      // line tasks per phase, n^(dim-1)
+  int Lv = 0;     // pairs per line, q(q+1)/2
+  int S12 = 0;    // number of (alpha1, alpha2) pairs (tetrahedra)
+  int nvp = 0, nfp = 0;          // volume / facet pairs per element
+  int fph_off[4] = {0, 0, 0, 0}; // offsets (in doubles) of the facet pair phases in fdir
+  int fph_len[4] = {0, 0, 0, 0}; // facet pairs per task in each phase
+  std::vector<double> eta[3], w1[3];
+  std::vector<double> dl[3];          // dl[k][a*n+b] = d ell_{k,b}/d eta (eta_{k,a})
+  std::vector<double> l1m, l1p, l2m, l3m, L2J;
+  std::vector<double> psi1, psi2, psi3;
+  std::vector<int> ints;              // off1[p+1] | s12_a1[S12] | moff[S12] | mode_s12[Np] (tri: mode_a1[Np])
+  int i_off1 = 0, i_s12a1 = 0, i_moff = 0, i_mode = 0;
+  std::vector<double> wvol;           // [Nq]
+  std::vector<double> wfac;           // [Nfn]
+  std::vector<double> xi_vol, xi_fac; // [Nq*dim], [Nfn*dim]
+  std::vector<double> deta;           // [Nq][3][3]: d eta_k / d xi_l at volume nodes (k-major)
+  double nhat[4][3] = {};
+};
+
+// Per-mesh host geometry (setup.cpp) ready to upload.
+struct HostMesh {
+  RefTables ref;
+  int64_t E = 0;
+  std::vector<double> vdir, fdir;     // [E][nvp*dim], [E][nfp*dim] (phase-major)
+  std::vector<double> wj, wdj;        // [E][Nq] W J and W / J (interpolated J)
+  std::vector<double> bj, nrm;        // [E][Nfn], [E][dim][Nfn]
+  std::vector<int32_t> nbr_e, nbr_f;  // [E][Nfn]
+  std::vector<double> xvol;           // [E][Nq][dim]
+};
+
+esd_status build_ref(int dim, int p, RefTables* out, std::string* err);
+esd_status build_host_mesh(const esd_mesh_desc& d, HostMesh* out, std::string* err);
+
+// Device views passed to kernels by value.
+struct DevRef {
+  int dim, p, n, Nq, Np, Nf, Nqf, Nfn, Ntot, T, Lv, S12, nvp, nfp;
+  int fph_off[4], fph_len[4];
+  const double *psi1, *psi2, *psi3;
+  const int *off1, *s12a1, *moff, *mode;
+  const double *l1m, *l1p, *l2m, *l3m, *L2J;
+  const double* wvol;
+};
+
+struct DevMesh {
+  int64_t E;
+  const double *vdir, *fdir, *wj, *wdj, *bj, *nrm;
+  const int32_t *nbr_e, *nbr_f;
+  double* states;   // [E][nfields][Ntot]
+  double* cfac;     // [E][Nfn] sound speed at facet nodes
+  int* flag;        // admissibility flag
+  double gamma;
+  int lf;
+};
+
+struct LaunchCfg {
+  int ea = 1, ta = 128;  size_t sa = 0;   // projection kernel: elements/CTA, threads, smem bytes
+  int eb = 1, tb = 128;  size_t sb = 0;   // residual kernel
+  int ev = 1, tv = 128;  size_t sv = 0;   // residual adjoint kernel
+};
+
+// RK epilogue of the residual kernel: acc_out = acc_in + cb*k, stage_out = u0 + ca*k.
+struct Epilogue {
+  int mode;                 // 0: store dudt; 1: RK stage update; 2: diagnostics partials
+  double* dudt;
+  const double* u0;
+  const double* acc_in;
+  double* acc_out;
+  double* stage_out;
+  double ca, cb;
+  double* diag;             // [E][nc+2] partial sums (mode 2)
+};
+
+// batched execution: one entry per mesh, one per (mesh, element tile)
+struct BatchMesh {
+  DevRef R;
+  DevMesh M;
+  const double* u;   // stage input for the projection
+  Epilogue ep;       // residual epilogue (RK update)
+};
+struct BatchItem {
+  int mesh;
+  int E;
+  int64_t e0;
+};
+
+LaunchCfg choose_launch(const RefTables& r);
+size_t smem_project(const RefTables& r, int e);
+size_t smem_residual(const RefTables& r, int e);
+
+// Kernel launchers (kernels.cu).  All return cudaGetLastError().
+cudaError_t launch_project(const DevRef& R, const DevMesh& M, const LaunchCfg& L, const double* u,
+                           double* w_modal, cudaStream_t s);
+cudaError_t launch_residual(const DevRef& R, const DevMesh& M, const LaunchCfg& L, const Epilogue& ep,
+                            cudaStream_t s);
+cudaError_t launch_l2_project(const DevRef& R, const DevMesh& M, const double* un, double* um,
+                              cudaStream_t s);
+cudaError_t launch_vjp(const DevRef& R, const DevMesh& M, const LaunchCfg& L, const double* u, const double* cot,
+                       double* grad, double* qbar, double* qext, cudaStream_t s);
+cudaError_t launch_axpby(double* out, double a, const double* x, double b, const double* y, int64_t n,
+                         cudaStream_t s);
+cudaError_t launch_batch(int dim, int stage, const BatchMesh* meshes, const BatchItem* items, int nitems,
+                         int grid, int threads, size_t smem, cudaStream_t s);
+cudaError_t launch_reduce_diag(const double* part, int64_t E, int ncol, double* out, cudaStream_t s);
+cudaError_t launch_copy(const double* src, double* dst, int64_t n, cudaStream_t s);
+cudaError_t measure_fp64(double* flops, cudaStream_t s);
+cudaError_t set_smem_limits(const LaunchCfg& L, int dim);
+
+}  // namespace esd

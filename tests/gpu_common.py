@@ -1,0 +1,110 @@
+"""Shared helpers for the GPU tests: seeded workloads, the oracle side, and the CUDA side."""
+from functools import lru_cache
+
+import numpy as np
+
+import esd_inputs as I
+from oracle.residual import Discretization
+
+
+def rel_err_per_var(got, ref):
+    """max |got - ref| / max |ref| for each conserved variable (axis 1 of [E, Nc, Np]); a
+    variable whose reference is identically zero is measured against the largest variable."""
+    got = np.asarray(got)
+    ref = np.asarray(ref)
+    num = np.abs(got - ref).max(axis=(0, 2))
+    den = np.abs(ref).max(axis=(0, 2))
+    den = np.where(den > 0, den, den.max())
+    return num / den
+
+
+@lru_cache(maxsize=None)
+def workload(dim, M, p, warp=True, flux="LF", state=None, noise=1e-3, L=None):
+    """Oracle discretisation and a seeded modal state (reference L2 projection of the analytic
+    state, Section 7.4/7.5, plus seeded N(0, noise) on every mode)."""
+    L = L if L is not None else 2 * np.pi
+    state = state or ("vortex" if dim == 2 else "tgv")
+    mesh, X = I.config_mesh(dim, M, L, p, warp)
+    D = Discretization(dim, p, X, mesh.nbr_elem, mesh.nbr_face, flux=flux)
+    f = I.config_state_fn(dim, L, state)
+    u0 = f(D.geo.x_vol)
+    um = np.einsum("ij,i,eic->ecj", D.V, D.ref.w, u0)
+    if noise:
+        um = um + I.seeded_normal(11 + 7 * p + dim, um.shape, noise)
+    return mesh, X, D, np.ascontiguousarray(um)
+
+
+def gpu_mesh(dim, p, X, mesh, flux="LF"):
+    import paper_2312_07874_gb300 as E
+    return E.Mesh(dim, p, X, mesh.nbr_elem, mesh.nbr_face, flux=flux)
+
+
+def to_dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+
+
+# ---------------------------------------------------------------------------------------
+# Parity tolerance derived from the arithmetic.
+#
+# The bound is 1e-12 relative max-norm per conserved variable, except where the
+# output's own FP64 conditioning is worse: kappa_e is the largest relative change of
+# variable e of d u~/dt (oracle) when its inputs -- the modal state and the mapping
+# nodes -- or the projected entropy variables entering U(w) are perturbed by one unit
+# roundoff (seeded, relative).  Two independent
+# FP64 implementations then differ by a small multiple of kappa_e; the bound used is
+# max(1e-12, 20 kappa_e).  A real defect (dropped term, sign, index) gives O(1)
+# relative errors, orders of magnitude above either bound.
+# ---------------------------------------------------------------------------------------
+PARITY_TOL = 1e-12
+KAPPA_FACTOR = 20.0
+
+
+class perturbed_entropy_inversion:
+    """Context manager: the oracle's U(w) sees its argument perturbed by one unit roundoff
+    (relative, seeded) -- the rounding of the projected entropy variables, where the
+    low-Mach states are most sensitive."""
+
+    def __init__(self, seed):
+        self.rng = np.random.default_rng(seed)
+
+    def __enter__(self):
+        from oracle import euler
+        self.orig = euler.cons_from_entropy
+        eps = np.finfo(float).eps / 2
+
+        def pert(w, gamma=euler.GAMMA):
+            return self.orig(w * (1 + eps * self.rng.standard_normal(w.shape)), gamma)
+        euler.cons_from_entropy = pert
+        return self
+
+    def __exit__(self, *a):
+        from oracle import euler
+        euler.cons_from_entropy = self.orig
+
+
+def ulp_sensitivity(D, um, ref, elems=None, mesh=None, X=None, flux="LF"):
+    """kappa_e: largest relative change of d u~/dt (per variable) under one-unit-roundoff
+    perturbations of (a) the modal state, (b) the mapping nodes, (c) the projected entropy
+    variables entering U(w)."""
+    rng = np.random.default_rng(12345)
+    eps = np.finfo(float).eps / 2
+    k = [rel_err_per_var(D.rhs(um * (1 + eps * rng.standard_normal(um.shape)), "sparse", elems=elems), ref)]
+    if X is not None:
+        D2 = Discretization(D.dim, D.p, X * (1 + eps * rng.standard_normal(X.shape)), mesh.nbr_elem,
+                            mesh.nbr_face, flux=flux)
+        k.append(rel_err_per_var(D2.rhs(um, "sparse", elems=elems), ref))
+    with perturbed_entropy_inversion(99):
+        k.append(rel_err_per_var(D.rhs(um, "sparse", elems=elems), ref))
+    return np.max(np.stack(k), axis=0)
+
+
+@lru_cache(maxsize=None)
+def sensitivity(dim, M, p, warp=True, flux="LF", state=None, noise=1e-3):
+    mesh, X, D, um = workload(dim, M, p, warp, flux, state, noise)
+    ref = D.rhs(um, "sparse")
+    return ref, ulp_sensitivity(D, um, ref, None, mesh, X, flux)
+
+
+def parity_bound(kappa):
+    return np.maximum(PARITY_TOL, KAPPA_FACTOR * np.asarray(kappa))

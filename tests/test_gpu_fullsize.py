@@ -1,0 +1,51 @@
+"""Parity at the benchmark sizes, in the benchmark's launch configuration, on sampled
+outputs: the GPU computes d u~/dt on the full mesh; the oracle computes the same
+quantity for a seeded sample of elements one by one."""
+from functools import lru_cache
+
+import numpy as np
+import pytest
+
+import esd_inputs as I
+from oracle.residual import Discretization
+from gpu_common import to_dev, rel_err_per_var, ulp_sensitivity, parity_bound
+
+pytestmark = pytest.mark.gpu
+
+
+@lru_cache(maxsize=None)
+def full(dim, M, L, p, state, warp=True, flux="LF"):
+    mesh, X = I.config_mesh(dim, M, L, p, warp)
+    D = Discretization(dim, p, X, mesh.nbr_elem, mesh.nbr_face, flux=flux)
+    f = I.config_state_fn(dim, L, state)
+    um = np.einsum("ij,i,eic->ecj", D.V, D.ref.w, f(D.geo.x_vol))
+    if dim == 2:   # U(-1e-3, 1e-3) on nodal density before projection (config recipe)
+        nod = f(D.geo.x_vol)
+        nod[..., 0] += I.seeded_uniform(1, nod[..., 0].shape, -1e-3, 1e-3)
+        um = np.einsum("ij,i,eic->ecj", D.V, D.ref.w, nod)
+    return mesh, X, D, np.ascontiguousarray(um)
+
+
+@pytest.mark.parametrize("dim,M,L,p,state", [(3, 16, 2 * np.pi, 4, "tgv"), (2, 64, 1.0, 4, "vortex"),
+                                             (2, 64, 1.0, 8, "vortex")])
+def test_fullsize_sampled(dim, M, L, p, state):
+    import torch
+    import paper_2312_07874_gb300 as E
+    mesh, X, D, um = full(dim, M, L, p, state)
+    gm = E.Mesh(dim, p, X, mesh.nbr_elem, mesh.nbr_face, flux="LF")
+    got = gm.rhs(to_dev(um)).cpu().numpy()
+    gm.check()
+    rng = np.random.default_rng(2024)
+    sample = np.sort(rng.choice(D.E, size=24, replace=False))
+    ref = D.rhs(um, "sparse", elems=sample)
+    err = rel_err_per_var(got[sample], ref)
+    # one-ulp sensitivity of the sampled outputs (state, mapping nodes, entropy variables)
+    kappa = ulp_sensitivity(D, um, ref, elems=sample, mesh=mesh, X=X)
+    bound = parity_bound(kappa)
+    print(f"full-size dim={dim} M={M} p={p}: err={err} kappa={kappa}")
+    assert np.all(err < bound), (err, kappa)
+    # whole-mesh invariants on the GPU output: conservation (Theorem 2)
+    cons = D.conservation_rate(got)
+    y = np.einsum("ij,ecj->eic", D.V, got)
+    scale = np.einsum("i,ei,eic->c", D.ref.w, D.geo.J_vol, np.abs(y))
+    assert np.all(np.abs(cons) < 1e-12 * scale)

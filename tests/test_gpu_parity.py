@@ -1,0 +1,170 @@
+"""GPU parity: the CUDA path through the C ABI against the oracle, element by element.
+
+Tolerance: 1e-12 relative max-norm per conserved variable (FP64 on both sides)."""
+import numpy as np
+import pytest
+
+from gpu_common import workload, gpu_mesh, to_dev, rel_err_per_var, sensitivity, parity_bound
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+
+# (dim, M, p, state): several residual tiles plus a ragged tail at each degree
+RHS_CASES = [(2, 3, 1, "vortex"), (2, 5, 2, "vortex"), (2, 8, 3, "vortex"), (2, 8, 4, "vortex"),
+             (2, 4, 6, "vortex"), (2, 3, 8, "vortex"), (2, 3, 10, "vortex"),
+             (3, 3, 1, "density_wave"), (3, 3, 2, "density_wave"), (3, 3, 3, "density_wave"),
+             (3, 3, 4, "density_wave"), (3, 3, 2, "tgv"), (3, 3, 3, "tgv"), (3, 3, 4, "tgv")]
+
+
+@pytest.mark.parametrize("dim,M,p,state", RHS_CASES)
+@pytest.mark.parametrize("flux", ["LF", "EC"])
+def test_rhs_parity(dim, M, p, state, flux):
+    """esd_rhs vs the oracle's sparse route on every element; bound: 1e-12 relative per
+    variable, or 20 x the oracle's own one-ulp sensitivity where that is larger."""
+    import torch
+    mesh, X, D, um = workload(dim, M, p, True, flux, state)
+    ref, kappa = sensitivity(dim, M, p, True, flux, state)
+    gm = gpu_mesh(dim, p, X, mesh, flux)
+    u = to_dev(um)
+    out = gm.rhs(u)
+    torch.cuda.synchronize()
+    gm.check()
+    err = rel_err_per_var(out.cpu().numpy(), ref)
+    print(f"parity dim={dim} p={p} {state} {flux}: err={err} kappa={kappa}")
+    assert np.all(err < parity_bound(kappa)), (err, kappa)
+
+
+@pytest.mark.parametrize("dim,M,p", [(2, 5, 2), (2, 4, 5), (3, 3, 2), (3, 3, 4)])
+def test_entropy_projection_parity(dim, M, p):
+    import torch
+    mesh, X, D, um = workload(dim, M, p)
+    ref = np.transpose(D.project_entropy(um), (0, 2, 1))
+    gm = gpu_mesh(dim, p, X, mesh)
+    w = gm.project_entropy(to_dev(um))
+    torch.cuda.synchronize()
+    err = rel_err_per_var(w.cpu().numpy(), ref)
+    assert np.all(err < TOL), err
+
+
+@pytest.mark.parametrize("dim,M,p", [(2, 4, 3), (3, 3, 3)])
+def test_l2_projection_and_nodes(dim, M, p):
+    import torch
+    import esd_inputs as I
+    mesh, X, D, um = workload(dim, M, p)
+    gm = gpu_mesh(dim, p, X, mesh)
+    x = gm.volume_nodes()
+    f = I.config_state_fn(dim, 2 * np.pi, "vortex" if dim == 2 else "tgv")
+    un = np.transpose(f(x), (0, 2, 1))                       # [E, Nc, Nq] library node order
+    got = gm.l2_project(to_dev(un))
+    torch.cuda.synchronize()
+    ref = np.einsum("ij,i,eic->ecj", D.V, D.ref.w, f(D.geo.x_vol))
+    err = rel_err_per_var(got.cpu().numpy(), ref)
+    assert np.all(err < TOL), err
+
+
+@pytest.mark.parametrize("dim,M,p", [(2, 5, 3), (3, 3, 2)])
+def test_rk4_step_parity(dim, M, p):
+    import torch
+    from oracle.timestep import rk4_step
+    state = "vortex" if dim == 2 else "density_wave"
+    mesh, X, D, um = workload(dim, M, p, True, "LF", state)
+    dt = 1e-3
+    ref = rk4_step(lambda v: D.rhs(v, "sparse"), um, dt)
+    gm = gpu_mesh(dim, p, X, mesh)
+    u = to_dev(um)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        gm.rk_step(u, dt)           # captured into a graph on a non-default stream
+        ck = torch.empty((4,) + u.shape, dtype=torch.float64, device="cuda")
+        u2 = to_dev(um)
+        gm.rk_step(u2, dt, ck)
+    s.synchronize()
+    _, kappa = sensitivity(dim, M, p, True, "LF", state)
+    for got in (u, u2):
+        err = rel_err_per_var(got.cpu().numpy() - um, ref - um)   # compare the increments
+        assert np.all(err < parity_bound(kappa)), (err, kappa)
+    # checkpoints hold the four stage inputs
+    k1 = D.rhs(um, "sparse")
+    assert np.all(rel_err_per_var(ck[0].cpu().numpy(), um) < 1e-15)
+    assert np.all(rel_err_per_var(ck[1].cpu().numpy() - um, 0.5 * dt * k1) < parity_bound(kappa))
+
+
+def test_rk4_graph_replay_matches_direct():
+    import torch
+    mesh, X, D, um = workload(2, 4, 3)
+    gm = gpu_mesh(2, 3, X, mesh)
+    a, b = to_dev(um), to_dev(um)
+    s = torch.cuda.Stream()
+    for _ in range(3):
+        with torch.cuda.stream(s):
+            gm.rk_step(a, 2e-3)
+        import paper_2312_07874_gb300 as E
+        E.lib().esd_rk_step(gm.handle, E._ptr(b), 2e-3, None, None)   # legacy stream: direct launches
+        torch.cuda.synchronize()
+    assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("dim,M,p", [(2, 4, 3), (3, 3, 3)])
+def test_diagnostics_theorems(dim, M, p):
+    """Theorem 2 (conservation) and Theorem 4 (entropy conservation with EC facets) on the GPU."""
+    import torch
+    mesh, X, D, um = workload(dim, M, p, True, "EC")
+    gm = gpu_mesh(dim, p, X, mesh, "EC")
+    u = to_dev(um)
+    d = gm.diagnostics(u).cpu().numpy()
+    dudt = gm.rhs(u).cpu().numpy()
+    nc = dim + 2
+    scale = np.abs(d[nc + 1])
+    assert abs(d[nc]) < 1e-12 * scale
+    # the oracle's own statement of both theorems evaluated on the GPU's du/dt
+    ent, ent_scale = D.entropy_rate(um, dudt)
+    assert abs(ent) < 1e-12 * ent_scale
+    cons = D.conservation_rate(dudt)
+    y = np.einsum("ij,ecj->eic", D.V, dudt)
+    cscale = np.einsum("i,ei,eic->c", D.ref.w, D.geo.J_vol, np.abs(y))
+    assert np.all(np.abs(cons) < 1e-13 * cscale)
+    assert np.all(np.abs(d[:nc]) < 1e-12 * cscale * 10)
+
+
+@pytest.mark.parametrize("dim,p", [(2, 4), (3, 3)])
+def test_free_stream_gpu(dim, p):
+    import torch
+    from oracle import euler
+    mesh, X, D, _ = workload(dim, 3, p)
+    ubar = euler.conservative(np.array(1.3), np.array([0.4, -0.7, 0.2][:dim]), np.array(2.1))
+    um = np.einsum("ij,i,eic->ecj", D.V, D.ref.w, np.broadcast_to(ubar, (D.E, D.ref.Nq, D.Nc)))
+    gm = gpu_mesh(dim, p, X, mesh)
+    out = gm.rhs(to_dev(um)).cpu().numpy()
+    assert np.abs(out).max() < 1e-12 * np.abs(ubar).max()
+
+
+def test_invalid_arguments_rejected_before_launch():
+    import torch
+    import paper_2312_07874_gb300 as E
+    mesh, X, D, um = workload(2, 3, 2)
+    gm = gpu_mesh(2, 2, X, mesh)
+    u = to_dev(um)
+    host = np.zeros(um.shape)
+    st = E.lib().esd_rhs(gm.handle, E.ctypes.c_void_p(host.ctypes.data), E._ptr(u), None)
+    assert st == -1
+    st = E.lib().esd_rhs(gm.handle, E._ptr(u), E._ptr(u), None)   # aliasing
+    assert st == -1
+    st = E.lib().esd_rk_step(gm.handle, E._ptr(u), -1.0, None, None)
+    assert st == -1
+
+
+def test_non_admissible_state_flagged():
+    """A negative density in the input is reported as ESD_ERR_STATE by esd_mesh_check
+    (host-side detection of a device flag; nothing faults)."""
+    import torch
+    import paper_2312_07874_gb300 as E
+    mesh, X, D, um = workload(2, 3, 2)
+    gm = gpu_mesh(2, 2, X, mesh)
+    bad = um.copy()
+    bad[3, 0, 0] = -abs(bad[3, 0, 0]) * 3
+    gm.rhs(to_dev(bad))
+    with pytest.raises(E.EsdError) as ex:
+        gm.check()
+    assert ex.value.status == -4
+    gm.rhs(to_dev(um))
+    gm.check()

@@ -1,0 +1,137 @@
+"""The hand-written adjoint (esd_rhs_vjp, esd_rk_step_vjp, autograd rollout) against the
+oracle's complex-step Jacobian and against central differences of the GPU forward."""
+import numpy as np
+import pytest
+
+from gpu_common import workload, gpu_mesh, to_dev
+from oracle.jacobian import jvp, local_vjp, rk4_jvp
+
+pytestmark = pytest.mark.gpu
+
+CASES = [(2, 3, 2, "vortex"), (2, 4, 4, "vortex"), (3, 3, 2, "density_wave"), (3, 3, 3, "density_wave"),
+         (3, 3, 3, "tgv")]
+
+
+@pytest.mark.parametrize("dim,M,p,state", CASES)
+@pytest.mark.parametrize("flux", ["LF", "EC"])
+def test_vjp_dot_product_against_oracle(dim, M, p, state, flux):
+    """<c, J v> (oracle, complex step: exact to rounding) = <J^T c, v> (GPU adjoint)."""
+    import torch
+    mesh, X, D, um = workload(dim, M, p, True, flux, state)
+    rng = np.random.default_rng(7)
+    c = rng.standard_normal(um.shape)
+    v = rng.standard_normal(um.shape)
+    jv = jvp(D, um, v)
+    gm = gpu_mesh(dim, p, X, mesh, flux)
+    import paper_2312_07874_gb300 as E
+    g = torch.empty((D.E, D.Nc, D.Np), dtype=torch.float64, device="cuda")
+    E.esd_rhs_vjp(gm.handle, to_dev(um), to_dev(c), g)
+    torch.cuda.synchronize()
+    lhs = np.sum(c * jv)
+    rhs = np.sum(g.cpu().numpy() * v)
+    scale = np.sum(np.abs(c * jv))
+    assert abs(lhs - rhs) < 1e-11 * scale, (lhs, rhs, scale)
+
+
+@pytest.mark.parametrize("dim,M,p,state", [(2, 3, 2, "vortex"), (3, 3, 2, "density_wave"), (3, 3, 3, "tgv")])
+def test_vjp_per_element_jacobian_transpose(dim, M, p, state):
+    """Per-element rows of J^T c equal the oracle's column-by-column Jacobian transpose."""
+    import torch
+    import paper_2312_07874_gb300 as E
+    mesh, X, D, um = workload(dim, M, p, True, "LF", state)
+    rng = np.random.default_rng(8)
+    c = rng.standard_normal(um.shape)
+    gm = gpu_mesh(dim, p, X, mesh)
+    g = torch.empty((D.E, D.Nc, D.Np), dtype=torch.float64, device="cuda")
+    E.esd_rhs_vjp(gm.handle, to_dev(um), to_dev(c), g)
+    g = g.cpu().numpy()
+    for e in (0, D.E // 2, D.E - 1):
+        ref = local_vjp(D, um, c, e)
+        assert np.abs(g[e] - ref).max() < 1e-10 * np.abs(ref).max(), e
+
+
+@pytest.mark.parametrize("dim,M,p,state", [(2, 4, 3, "vortex"), (3, 3, 3, "tgv")])
+def test_vjp_central_differences_of_gpu_forward(dim, M, p, state):
+    """Dot-product test against central differences of esd_rhs itself (h = 1e-6, 1e-6 relative)."""
+    import torch
+    import paper_2312_07874_gb300 as E
+    mesh, X, D, um = workload(dim, M, p, True, "LF", state)
+    gm = gpu_mesh(dim, p, X, mesh)
+    rng = np.random.default_rng(9)
+    c = to_dev(rng.standard_normal(um.shape))
+    v = to_dev(rng.standard_normal(um.shape))
+    u = to_dev(um)
+    h = 1e-6
+    fd = (gm.rhs(u + h * v) - gm.rhs(u - h * v)) / (2 * h)
+    g = torch.empty_like(u)
+    E.esd_rhs_vjp(gm.handle, u, c, g)
+    lhs = float((c * fd).sum())
+    rhs = float((g * v).sum())
+    assert abs(lhs - rhs) < 1e-6 * float((c * fd).abs().sum())
+
+
+@pytest.mark.parametrize("dim,M,p,state", [(2, 3, 2, "vortex"), (3, 3, 2, "density_wave")])
+def test_rk_step_vjp_against_oracle(dim, M, p, state):
+    import torch
+    import paper_2312_07874_gb300 as E
+    mesh, X, D, um = workload(dim, M, p, True, "LF", state)
+    gm = gpu_mesh(dim, p, X, mesh)
+    dt = 2e-3
+    rng = np.random.default_rng(10)
+    c = rng.standard_normal(um.shape)
+    v = rng.standard_normal(um.shape)
+    u = to_dev(um)
+    ck = torch.empty((4,) + u.shape, dtype=torch.float64, device="cuda")
+    gm.rk_step(u, dt, ck)
+    cin = torch.empty_like(u)
+    E.esd_rk_step_vjp(gm.handle, ck, dt, to_dev(c), cin)
+    jv = rk4_jvp(D, um, v, dt)
+    lhs = np.sum(c * jv)
+    rhs = np.sum(cin.cpu().numpy() * v)
+    assert abs(lhs - rhs) < 1e-11 * np.sum(np.abs(c * jv))
+    # in place (cot_in aliases cot_out)
+    cc = to_dev(c)
+    E.esd_rk_step_vjp(gm.handle, ck, dt, cc, cc)
+    assert torch.allclose(cc, cin, rtol=0, atol=0)
+
+
+@pytest.mark.parametrize("checkpoint", ["stages", "steps"])
+def test_rollout_gradient_central_differences(checkpoint):
+    """20-step RK4 rollout through torch.autograd with per-stage checkpoints; gradient of
+    <w, u_N> against central differences (h = 1e-6, 1e-6 relative)."""
+    import torch
+    from paper_2312_07874_gb300.autograd import rollout
+    mesh, X, D, um = workload(3, 3, 3, True, "LF", "tgv")
+    gm = gpu_mesh(3, 3, X, mesh)
+    dt = 2e-3
+    rng = np.random.default_rng(11)
+    w = to_dev(rng.standard_normal(um.shape))
+    v = to_dev(rng.standard_normal(um.shape))
+    u0 = to_dev(um).requires_grad_(True)
+    loss = (w * rollout(u0, gm, dt, 20, checkpoint)).sum()
+    loss.backward()
+    g = u0.grad
+    h = 1e-6
+
+    def L(x):
+        with torch.no_grad():
+            return float((w * rollout(x, gm, dt, 20, checkpoint)).sum())
+    fd = (L(to_dev(um) + h * v) - L(to_dev(um) - h * v)) / (2 * h)
+    ad = float((g * v).sum())
+    assert abs(fd - ad) < 1e-6 * abs(ad), (fd, ad)
+
+
+def test_vjp_torch_function():
+    import torch
+    from paper_2312_07874_gb300.autograd import Rhs
+    mesh, X, D, um = workload(2, 3, 2, True, "LF", "vortex")
+    gm = gpu_mesh(2, 2, X, mesh)
+    u = to_dev(um).requires_grad_(True)
+    out = Rhs.apply(u, gm)
+    rng = np.random.default_rng(12)
+    c = to_dev(rng.standard_normal(um.shape))
+    (out * c).sum().backward()
+    v = rng.standard_normal(um.shape)
+    jv = jvp(D, um, v)
+    assert abs(float((u.grad.cpu() * torch.from_numpy(v)).sum()) - np.sum(c.cpu().numpy() * jv)) < \
+        1e-11 * np.sum(np.abs(c.cpu().numpy() * jv))
