@@ -128,6 +128,27 @@ esd_status esd_project_entropy(esd_mesh mesh, const double* u, double* w_modal, 
  * Eq. (interface_flux).  u, dudt: device, [n_elem][N_c][N_p*]; u and dudt must not alias. */
 esd_status esd_rhs(esd_mesh mesh, const double* u, double* dudt, void* stream);
 
+/* esd_rhs for callers that cannot allocate device memory (the paper has no counterpart).
+ *
+ * Some callers cannot call cudaMalloc: plug-ins running inside a host application that
+ * owns the whole device-memory budget through its own allocator, or fixed-footprint
+ * deployments that forbid any allocation after start-up.  This entry point computes
+ * exactly what esd_rhs computes, with the same kernels, but takes the per-node state
+ * scratch (entropy-projected states and facet sound speeds) from a fixed array in device
+ * global memory that the library reserves on every GPU when it is loaded (32 MiB, held
+ * until the process exits) instead of from the mesh's workspace.  It allocates nothing.
+ * The caller still passes the inputs (mesh, u) and the output (dudt).
+ * - Limit: the mesh needs n_elem * ((dim+5) * (N_q + N_f*N_fq) + N_f*N_fq) doubles of
+ *   scratch (about 15 KB per element for tetrahedra at p = 4, 2.4 KB for triangles at
+ *   p = 4); larger meshes are rejected with ESD_ERR_UNSUPPORTED before any launch.
+ * - The first call on a device looks up the array's device address (once per device,
+ *   with that device current); make that first call before any stream capture.
+ * - Every call shares the one array and leaves the last call's contents in it.  Nothing
+ *   in it needs to start at zero (each call overwrites every value it reads), but calls
+ *   that overlap on the GPU (different streams, or concurrent host threads) race on it.
+ * u, dudt: device [n_elem][N_c][N_p*]; they must not alias. */
+esd_status esd_rhs_static_scratch(esd_mesh mesh, const double* u, double* dudt, void* stream);
+
 /* Vector-Jacobian product of esd_rhs with respect to u: grad = (d rhs / d u)^T cot.
  * The paper has no counterpart (it is the adjoint of Eq. (dudt_modal)).  u, cot, grad:
  * device [n_elem][N_c][N_p*]; grad must not alias u or cot. */

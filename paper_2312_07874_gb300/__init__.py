@@ -49,6 +49,7 @@ SYMBOLS = {
     "esd_project_entropy": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
     "esd_rhs": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
     "esd_rhs_vjp": ([ctypes.c_void_p] * 5, ctypes.c_int),
+    "esd_rhs_static_scratch": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
     "esd_rk_step": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
     "esd_rk_step_vjp": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
                          ctypes.c_void_p], ctypes.c_int),
@@ -179,6 +180,11 @@ def esd_project_entropy(h, u, w_modal, stream=None):
 
 def esd_rhs(h, u, dudt, stream=None):
     _check(lib().esd_rhs(h, _ptr(u), _ptr(dudt), _stream(stream)))
+
+
+def esd_rhs_static_scratch(h, u, dudt, stream=None):
+    """esd_rhs without any allocation: state scratch from the library's fixed device array."""
+    _check(lib().esd_rhs_static_scratch(h, _ptr(u), _ptr(dudt), _stream(stream)))
 
 
 def esd_rhs_vjp(h, u, cot, grad, stream=None):

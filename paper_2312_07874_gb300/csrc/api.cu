@@ -605,6 +605,72 @@ esd_status esd_batch_rk_step(esd_batch b, double* const* u, const double* dt, vo
   return batch_run(b, 1, ptrs, dts, (cudaStream_t)stream);
 }
 
+// ---------------------------------------------------------------------------
+// esd_rhs_static_scratch: the same two kernels as esd_rhs, with the per-node
+// state scratch taken from a fixed array in device global memory instead of
+// the mesh's workspace.  The array is reserved on every device when the
+// library loads and is held until the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr size_t kStaticScratchBytes = size_t(32) << 20;   // 32 MiB
+constexpr size_t kStaticScratchDoubles = kStaticScratchBytes / sizeof(double);
+static __device__ __align__(256) double g_static_scratch[kStaticScratchDoubles];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mutex;
+double* g_scratch_ptr[kMaxDevices] = {};
+
+// Device address of g_static_scratch on the current device.  In host code the
+// symbol's name is only a host-side stand-in, so the address is looked up once per
+// device (with that device current) and cached.
+esd_status static_scratch_address(double** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev < 0 || dev >= kMaxDevices) return fail(ESD_ERR_UNSUPPORTED, "device index out of range for the static scratch");
+  std::lock_guard<std::mutex> lock(g_scratch_mutex);
+  if (!g_scratch_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || p == nullptr) return cuda_fail(e, "cudaGetSymbolAddress(static scratch)");
+    g_scratch_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_scratch_ptr[dev];
+  return ESD_OK;
+}
+}  // namespace
+
+esd_status esd_rhs_static_scratch(esd_mesh m, const double* u, double* dudt, void* stream) {
+  if (!m) return fail(ESD_ERR_ARG, "null mesh");
+  esd_status st;
+  if ((st = check_dev(u, "u")) || (st = check_dev(dudt, "dudt"))) return st;
+  if (u == dudt) return fail(ESD_ERR_ARG, "u and dudt must not alias");
+  const size_t n_states = (size_t)m->E * nfields(m->dim) * m->ref.Ntot;
+  const size_t n_cfac = (size_t)m->E * m->ref.Nfn;
+  const size_t n_cfac_off = (n_states + 31) / 32 * 32;          // keep the second block 256-byte aligned
+  if (n_cfac_off + n_cfac > kStaticScratchDoubles) {
+    char msg[256];
+    std::snprintf(msg, sizeof msg,
+                  "mesh needs %zu bytes of state scratch; esd_rhs_static_scratch is limited to %zu bytes "
+                  "(use esd_rhs for larger meshes)",
+                  (n_cfac_off + n_cfac) * sizeof(double), kStaticScratchBytes);
+    return fail(ESD_ERR_UNSUPPORTED, msg);
+  }
+  double* scratch = nullptr;
+  if ((st = static_scratch_address(&scratch))) return st;
+  DevMesh M = m->M;
+  M.states = scratch;               // fully rewritten by the projection kernel before it is read
+  M.cfac = scratch + n_cfac_off;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = launch_project(m->R, M, m->L, u, nullptr, s);
+  if (e) return cuda_fail(e, "project launch");
+  Epilogue ep{};
+  ep.mode = 0;
+  ep.dudt = dudt;
+  e = launch_residual(m->R, M, m->L, ep, s);
+  return e ? cuda_fail(e, "residual launch") : ESD_OK;
+}
+
 esd_status esd_launch_stage(esd_mesh m, int stage, const double* u, double* out, void* stream) {
   if (!m) return fail(ESD_ERR_ARG, "null mesh");
   cudaStream_t s = (cudaStream_t)stream;
