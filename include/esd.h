@@ -181,6 +181,13 @@ esd_status esd_batch_rhs(esd_batch batch, const double* const* u, double* const*
 /* One RK4 step of every mesh; dt[i] is a HOST array of step sizes. */
 esd_status esd_batch_rk_step(esd_batch batch, double* const* u, const double* dt, void* stream);
 
+/* Autotuner (not in the paper): time the projection kernel over elements-per-CTA x
+ * threads-per-CTA and the residual kernel over elements-per-CTA on this mesh and state u
+ * (device, [n_elem][N_c][N_p*], admissible), keep the fastest, and drop captured RK4
+ * graphs.  Per-element arithmetic is independent of the tiling, so results are unchanged.
+ * Synchronous.  Batches built afterwards use the tuned tiles. */
+esd_status esd_autotune(esd_mesh mesh, const double* u, void* stream);
+
 /* Measurement hook: launch one kernel of the esd_rhs pipeline alone, so that it can be
  * timed with events on `stream`.  stage 0: the projection kernel on u (entropy projection
  * and entropy-projected states at all nodes, written to the handle's workspace; `out`

@@ -60,6 +60,7 @@ SYMBOLS = {
                        ctypes.c_void_p], ctypes.c_int),
     "esd_batch_rk_step": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_double),
                            ctypes.c_void_p], ctypes.c_int),
+    "esd_autotune": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
     "esd_launch_stage": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
                          ctypes.c_int),
     "esd_measure_fp64_peak": ([ctypes.POINTER(ctypes.c_double), ctypes.c_void_p], ctypes.c_int),
@@ -204,6 +205,10 @@ def esd_diagnostics(h, u, out, stream=None):
     _check(lib().esd_diagnostics(h, _ptr(u), _ptr(out), _stream(stream)))
 
 
+def esd_autotune(h, u, stream=None):
+    _check(lib().esd_autotune(h, _ptr(u), _stream(stream)))
+
+
 def esd_launch_stage(h, stage, u=None, out=None, stream=None):
     _check(lib().esd_launch_stage(h, int(stage), _ptr(u) if u is not None else None,
                                   _ptr(out) if out is not None else None, _stream(stream)))
@@ -297,3 +302,8 @@ class Mesh:
 
     def check(self):
         esd_mesh_check(self.handle)
+
+    def autotune(self, u):
+        esd_autotune(self.handle, u)
+        self.info = esd_mesh_info(self.handle)
+        return self.info

@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -156,6 +157,7 @@ esd_status esd_mesh_create(const esd_mesh_desc* d, esd_mesh* out) {
   R.psi1 = dtab + o_psi1; R.psi2 = dtab + o_psi2; R.psi3 = dtab + o_psi3;
   R.l1m = dtab + o_l1m; R.l1p = dtab + o_l1p; R.l2m = dtab + o_l2m; R.l3m = dtab + o_l3m; R.L2J = dtab + o_L2J;
   R.wvol = dtab + o_w;
+  R.dense_minv = r.dense_minv;
   R.off1 = itab + r.i_off1; R.s12a1 = itab + r.i_s12a1; R.moff = itab + r.i_moff; R.mode = itab + r.i_mode;
   // per-element data
   DevMesh& M = m->M;
@@ -171,6 +173,15 @@ esd_status esd_mesh_create(const esd_mesh_desc* d, esd_mesh* out) {
     return st;
   }
   M.vdir = vdir; M.fdir = fdir; M.wj = wj; M.wdj = wdj; M.bj = bj; M.nrm = nrm; M.nbr_e = ne; M.nbr_f = nf;
+  M.minv = nullptr;
+  if (r.dense_minv) {
+    double* mi = nullptr;
+    if ((st = m->upload(&mi, H.minv))) {
+      delete m;
+      return st;
+    }
+    M.minv = mi;
+  }
   const size_t nstate = (size_t)m->E * nfields(r.dim) * r.Ntot;
   const size_t nmodal = (size_t)m->E * m->nc * r.Np;
   if ((st = m->alloc(&M.states, nstate)) || (st = m->alloc(&M.cfac, (size_t)m->E * r.Nfn)) ||
@@ -386,7 +397,7 @@ esd_status esd_rk_step_vjp(esd_mesh m, const double* ck, double dt, const double
 }
 
 struct BatchGroup {
-  int dim = 0;
+  int dim = 0, p = 0;
   std::vector<int> members;          // indices into the batch's mesh list
   std::vector<BatchItem> pitems, ritems;
   BatchItem* d_pitems = nullptr;
@@ -430,11 +441,13 @@ esd_status esd_batch_create(const esd_mesh* meshes, int n, esd_batch* out) {
   esd_batch b = new esd_batch_s();
   b->meshes.assign(meshes, meshes + n);
   const int sms = sm_count();
-  for (int dim = 2; dim <= 3; ++dim) {
+  for (int key = 0; key < 2 * 16; ++key) {   // one group per (dimension, degree)
+    const int dim = 2 + key / 16, deg = key % 16;
     BatchGroup g;
     g.dim = dim;
+    g.p = deg;
     for (int i = 0; i < n; ++i) {
-      if (meshes[i]->dim != dim) continue;
+      if (meshes[i]->dim != dim || meshes[i]->p != deg) continue;
       esd_mesh m = meshes[i];
       const int mi = (int)g.members.size();
       g.members.push_back(i);
@@ -559,9 +572,11 @@ static esd_status batch_run(esd_batch b, int kind, const std::vector<const doubl
   for (int st = 0; st < nst && !e1; ++st)
     for (auto& g : b->groups) {
       BatchMesh* tab = G.d_tables[tix++];
-      if ((e1 = launch_batch(g.dim, 0, tab, g.d_pitems, (int)g.pitems.size(), g.pgrid, g.pthreads, g.psmem, cs)))
+      if ((e1 = launch_batch(g.dim, g.p + 1, 0, tab, g.d_pitems, (int)g.pitems.size(), g.pgrid, g.pthreads,
+                             g.psmem, cs)))
         break;
-      if ((e1 = launch_batch(g.dim, 1, tab, g.d_ritems, (int)g.ritems.size(), g.rgrid, g.rthreads, g.rsmem, cs)))
+      if ((e1 = launch_batch(g.dim, g.p + 1, 1, tab, g.d_ritems, (int)g.ritems.size(), g.rgrid, g.rthreads,
+                             g.rsmem, cs)))
         break;
     }
   e = cudaStreamEndCapture(cs, &graph);
@@ -669,6 +684,93 @@ esd_status esd_rhs_static_scratch(esd_mesh m, const double* u, double* dudt, voi
   ep.dudt = dudt;
   e = launch_residual(m->R, M, m->L, ep, s);
   return e ? cuda_fail(e, "residual launch") : ESD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner: elements per CTA (and threads for the projection) chosen by timing the
+// kernels on this mesh.  Every element is computed by the same per-element code
+// whatever the tiling, so the results do not depend on the choice.
+// ---------------------------------------------------------------------------
+static float time_launches(const std::function<cudaError_t()>& f, cudaStream_t s, int reps) {
+  if (f() != cudaSuccess) return 1e30f;   // warm-up
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  cudaEventRecord(a, s);
+  for (int i = 0; i < reps; ++i)
+    if (f() != cudaSuccess) {
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+      return 1e30f;
+    }
+  cudaEventRecord(b, s);
+  cudaEventSynchronize(b);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return ms / reps;
+}
+
+esd_status esd_autotune(esd_mesh m, const double* u, void* stream) {
+  if (!m) return fail(ESD_ERR_ARG, "null mesh");
+  esd_status st;
+  if ((st = check_dev(u, "u"))) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const RefTables& r = m->ref;
+  const size_t budget = 227 * 1024;
+  LaunchCfg best = m->L;
+  // projection: elements per CTA x threads
+  {
+    float tbest = 1e30f;
+    const int emax = std::max(1, (int)(budget / smem_project(r, 1)));
+    for (int e = emax; e >= 1; e = e > 1 ? e / 2 : 0) {
+      for (int thr : {128, 256, 512}) {
+        LaunchCfg L = m->L;
+        L.ea = e;
+        L.ta = thr;
+        L.sa = smem_project(r, e);
+        float t = time_launches([&] { return launch_project(m->R, m->M, L, u, nullptr, s); }, s, 3);
+        if (t < tbest) {
+          tbest = t;
+          best.ea = L.ea;
+          best.ta = L.ta;
+          best.sa = L.sa;
+        }
+      }
+      if (e == 1) break;
+    }
+  }
+  // residual: elements per CTA (threads follow: E * line tasks rounded to warps)
+  {
+    cudaError_t e0 = launch_project(m->R, m->M, best, u, nullptr, s);
+    if (e0) return cuda_fail(e0, "autotune projection");
+    Epilogue ep{};
+    ep.mode = 0;
+    ep.dudt = m->ws_adj[0];
+    float tbest = 1e30f;
+    const int emax = std::min(std::max(1, (int)(budget / smem_residual(r, 1))), std::max(1, 512 / r.T));
+    for (int e = 1; e <= emax; ++e) {
+      LaunchCfg L = best;
+      L.eb = e;
+      L.tb = std::max(64, ((e * r.T + 31) / 32) * 32);
+      L.sb = smem_residual(r, e);
+      float t = time_launches([&] { return launch_residual(m->R, m->M, L, ep, s); }, s, 3);
+      if (t < tbest) {
+        tbest = t;
+        best.eb = L.eb;
+        best.tb = L.tb;
+        best.sb = L.sb;
+      }
+    }
+  }
+  cudaError_t e = cudaStreamSynchronize(s);
+  cudaGetLastError();
+  if (e) return cuda_fail(e, "autotune");
+  m->L = best;
+  for (auto& g : m->graphs) cudaGraphExecDestroy(g.exec);   // captured graphs hold the old launch shapes
+  m->graphs.clear();
+  return ESD_OK;
 }
 
 esd_status esd_launch_stage(esd_mesh m, int stage, const double* u, double* out, void* stream) {

@@ -1,0 +1,1103 @@
+// Device-side building blocks shared by the kernel translation units: per-node
+// states, the two-point flux, sum-factorised transforms, the projection and
+// residual tiles, and the adjoint pieces.  Internal to the library.
+#pragma once
+
+#include <cmath>
+#include <cstdint>
+
+#include "esd_internal.h"
+
+namespace esd {
+
+// ---------------------------------------------------------------------------
+// Per-node state and the two-point flux (Section 7.2)
+// ---------------------------------------------------------------------------
+template <int D>
+struct NodeState {
+  double rho, v[D], p, beta, lrho, lbeta;
+};
+
+// fields are stored SoA: S[field*stride + idx]
+template <int D>
+__device__ __forceinline__ NodeState<D> load_state(const double* S, int stride, int idx) {
+  NodeState<D> s;
+  s.rho = S[idx];
+#pragma unroll
+  for (int k = 0; k < D; ++k) s.v[k] = S[(1 + k) * stride + idx];
+  s.p = S[(D + 1) * stride + idx];
+  s.beta = S[(D + 2) * stride + idx];
+  s.lrho = S[(D + 3) * stride + idx];
+  s.lbeta = S[(D + 4) * stride + idx];
+  return s;
+}
+
+// {{a}}_ln with per-node logarithms: for u = ((b-a)/(b+a))^2 < 1e-4 the series of
+// ln(b/a) = 2 artanh((b-a)/(b+a)) gives (a+b)/(2 + 2u/3 + 2u^2/5 + 2u^3/7);
+// otherwise (b-a)/(ln b - ln a).
+__device__ __forceinline__ double log_mean(double a, double b, double la, double lb) {
+  double s = a + b, d = b - a;
+  double f = d / s, u = f * f;
+  if (u < 1.0e-4) return s / (2.0 + u * (2.0 / 3.0 + u * (2.0 / 5.0 + u * (2.0 / 7.0))));
+  return d / (lb - la);
+}
+
+__device__ __forceinline__ double inv_log_mean(double a, double b, double la, double lb) {
+  double s = a + b, d = b - a;
+  double f = d / s, u = f * f;
+  if (u < 1.0e-4) return (2.0 + u * (2.0 / 3.0 + u * (2.0 / 5.0 + u * (2.0 / 7.0)))) / s;
+  return (lb - la) / d;
+}
+
+// Directional entropy-conservative flux f#(U^-,U^+,n) = sum_m n_m f_m^# (Eq. (ranocha_flux));
+// the energy component uses rho_ln {{v}}.n (v^-.v^+/2 + 1/((gamma-1){{rho/p}}_ln)) + (p^- v^+.n + p^+ v^-.n)/2.
+template <int D>
+__device__ __forceinline__ void ec_flux(const NodeState<D>& L, const NodeState<D>& R, const double* n,
+                                        double inv_gm1, double* F) {
+  double rho_ln = log_mean(L.rho, R.rho, L.lrho, R.lrho);
+  double ib_ln = inv_log_mean(L.beta, R.beta, L.lbeta, R.lbeta);
+  double vnL = 0.0, vnR = 0.0, vv = 0.0;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    vnL = fma(n[k], L.v[k], vnL);
+    vnR = fma(n[k], R.v[k], vnR);
+    vv = fma(L.v[k], R.v[k], vv);
+  }
+  double frho = rho_ln * 0.5 * (vnL + vnR);
+  double pavg = 0.5 * (L.p + R.p);
+  F[0] = frho;
+#pragma unroll
+  for (int k = 0; k < D; ++k) F[1 + k] = fma(frho, 0.5 * (L.v[k] + R.v[k]), pavg * n[k]);
+  F[D + 1] = fma(frho, fma(0.5, vv, inv_gm1 * ib_ln), 0.5 * (L.p * vnR + R.p * vnL));
+}
+
+// ---------------------------------------------------------------------------
+// FP64-lean evaluation of the same flux for the pair loops.
+//
+// * Reciprocals come from the MUFU approximation (rcp.approx.ftz.f64, another pipe)
+//   refined by Newton-Raphson steps x <- x + x (1 - a x), each of which squares the
+//   relative error: one step is enough where the result only enters a series
+//   correction, two steps give full double precision.
+// * The log-mean branch is chosen by an integer comparison of the bit patterns of
+//   u >= 0 and 1e-4 (same decision as the floating-point comparison, off the FP64 pipe).
+// * In the series branch, rho_ln = (a+b) G(u) with G = 1/(2F(u)) expanded to the same
+//   order, G = 1/2 - u/6 - 2u^2/45 - 22u^3/945 (differs from (a+b)/(2F) by < 1e-17
+//   relative for u < 1e-4); 1/((gamma-1) beta_ln) = K(u)/(a+b) with K = 2F/(gamma-1).
+// * Pair directions are stored halved (n/2), which absorbs the arithmetic means.
+// ---------------------------------------------------------------------------
+template <int NR>
+__device__ __forceinline__ double rcp_nr(double a) {
+  double x;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(x) : "d"(a));
+#pragma unroll
+  for (int i = 0; i < NR; ++i) {
+    const double e = fma(-a, x, 1.0);
+    x = fma(x, e, x);
+  }
+  return x;
+}
+
+__device__ __forceinline__ bool below_logmean_cutoff(double u) {
+  return __double_as_longlong(u) < 0x3F1A36E2EB1C432DLL;   // bit pattern of 1.0e-4
+}
+
+struct FluxK {
+  double inv_gm1;
+  double k0, k1, k2, k3;   // (2, 2/3, 2/5, 2/7) / (gamma - 1)
+};
+
+__device__ __forceinline__ FluxK make_fluxk(double gamma) {
+  FluxK K;
+  K.inv_gm1 = 1.0 / (gamma - 1.0);
+  K.k0 = 2.0 * K.inv_gm1;
+  K.k1 = (2.0 / 3.0) * K.inv_gm1;
+  K.k2 = (2.0 / 5.0) * K.inv_gm1;
+  K.k3 = (2.0 / 7.0) * K.inv_gm1;
+  return K;
+}
+
+// F = f#(L, R, 2 nh): the directional flux for the direction 2*nh.
+template <int D>
+__device__ __forceinline__ void ec_flux_fast(const NodeState<D>& L, const NodeState<D>& R, const double* nh,
+                                             const FluxK& K, double* F) {
+  // {{rho}}_ln.  The direct (log) formula is evaluated only when some lane of the warp
+  // needs it: for smooth states whole warps stay on the series, and the compiler cannot
+  // turn the rare branch into always-executed predicated code.
+  const unsigned active = __activemask();
+  const double s1 = L.rho + R.rho, d1 = R.rho - L.rho;
+  const double f1 = d1 * rcp_nr<1>(s1), u1 = f1 * f1;
+  const bool ser1 = below_logmean_cutoff(u1);
+  double rho_ln = s1 * fma(u1, fma(u1, fma(u1, -22.0 / 945.0, -2.0 / 45.0), -1.0 / 6.0), 0.5);
+  if (__any_sync(active, !ser1)) {
+    const double direct = d1 * rcp_nr<2>(R.lrho - L.lrho);
+    rho_ln = ser1 ? rho_ln : direct;
+  }
+  // 1 / ((gamma-1) {{rho/p}}_ln)
+  const double s2 = L.beta + R.beta, d2 = R.beta - L.beta;
+  const double r2 = rcp_nr<2>(s2);
+  const double f2 = d2 * r2, u2 = f2 * f2;
+  const bool ser2 = below_logmean_cutoff(u2);
+  double ibc = r2 * fma(u2, fma(u2, fma(u2, K.k3, K.k2), K.k1), K.k0);
+  if (__any_sync(active, !ser2)) {
+    const double direct = K.inv_gm1 * (R.lbeta - L.lbeta) * rcp_nr<2>(d2);
+    ibc = ser2 ? ibc : direct;
+  }
+  double vnL = 0.0, vnR = 0.0, vv = 0.0;   // vn = v.n/2
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    vnL = fma(nh[k], L.v[k], vnL);
+    vnR = fma(nh[k], R.v[k], vnR);
+    vv = fma(L.v[k], R.v[k], vv);
+  }
+  const double frho = rho_ln * (vnL + vnR);
+  const double hf = 0.5 * frho, ps = L.p + R.p;
+  F[0] = frho;
+#pragma unroll
+  for (int k = 0; k < D; ++k) F[1 + k] = fma(hf, L.v[k] + R.v[k], ps * nh[k]);
+  F[D + 1] = fma(frho, fma(0.5, vv, ibc), fma(L.p, vnR, R.p * vnL));
+}
+
+// ---------------------------------------------------------------------------
+// Sum-factorised PKD transforms (Section 5.2) on a tile of E elements.
+// Buffers are per element with stride `pe` (doubles); each holds N_c variables.
+// ---------------------------------------------------------------------------
+struct Tile {
+  double* base;   // shared memory
+  int pe;         // doubles per element
+  int E;          // elements in this tile
+};
+
+// out = V in  (modal -> nodal), using scratch s1 (and s2 for tetrahedra).  All buffers
+// distinct, except that for tetrahedra `out` may equal s1.
+template <int D>
+__device__ void apply_V(const DevRef& R, const Tile& t, int in, int s1, int s2, int out, int nc) {
+  const int n = R.n, p = R.p;
+  if (D == 2) {
+    int rows = (p + 1) * n, tot = t.E * nc * rows;
+    for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+      int row = idx % rows, ev = idx / rows, var = ev % nc, e = ev / nc;
+      int a1 = row / n, c2 = row % n;
+      const double* x = t.base + e * t.pe + in + var * R.Np;
+      int m0 = R.off1[a1];
+      double acc = 0.0;
+      for (int a2 = 0; a2 <= p - a1; ++a2) acc = fma(R.psi2[(m0 + a2) * n + c2], x[m0 + a2], acc);
+      t.base[e * t.pe + s1 + var * R.Nq + row] = acc;
+    }
+    __syncthreads();
+    rows = R.Nq;
+    tot = t.E * nc * rows;
+    for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+      int v = idx % rows, ev = idx / rows, var = ev % nc, e = ev / nc;
+      int c1 = v % n, c2 = v / n;
+      const double* y = t.base + e * t.pe + s1 + var * R.Nq;
+      double acc = 0.0;
+      for (int a1 = 0; a1 <= p; ++a1) acc = fma(R.psi1[a1 * n + c1], y[a1 * n + c2], acc);
+      t.base[e * t.pe + out + var * R.Nq + v] = acc;
+    }
+    __syncthreads();
+  } else {
+    // stage 1: contract alpha3 -> [s12][c3]   (into s1)
+    int rows = R.S12 * n, tot = t.E * nc * rows;
+    for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+      int row = idx % rows, ev = idx / rows, var = ev % nc, e = ev / nc;
+      int s = row / n, c3 = row % n;
+      int a1 = R.s12a1[s], a2 = s - R.off1[a1], m0 = R.moff[s];
+      const double* x = t.base + e * t.pe + in + var * R.Np;
+      double acc = 0.0;
+      for (int a3 = 0; a3 <= p - a1 - a2; ++a3) acc = fma(R.psi3[(m0 + a3) * n + c3], x[m0 + a3], acc);
+      t.base[e * t.pe + s1 + var * R.Nq + row] = acc;
+    }
+    __syncthreads();
+    // stage 2: contract alpha2 -> [a1][c2][c3]  (into s2)
+    rows = (p + 1) * n * n;
+    tot = t.E * nc * rows;
+    for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+      int row = idx % rows, ev = idx / rows, var = ev % nc, e = ev / nc;
+      int c3 = row % n, c2 = (row / n) % n, a1 = row / (n * n);
+      const double* y = t.base + e * t.pe + s1 + var * R.Nq;
+      int s0 = R.off1[a1];
+      double acc = 0.0;
+      for (int a2 = 0; a2 <= p - a1; ++a2) acc = fma(R.psi2[(s0 + a2) * n + c2], y[(s0 + a2) * n + c3], acc);
+      t.base[e * t.pe + s2 + var * R.Nq + row] = acc;
+    }
+    __syncthreads();
+    // stage 3: contract alpha1 -> nodal
+    rows = R.Nq;
+    tot = t.E * nc * rows;
+    for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+      int v = idx % rows, ev = idx / rows, var = ev % nc, e = ev / nc;
+      int c1 = v % n, c2 = (v / n) % n, c3 = v / (n * n);
+      const double* y = t.base + e * t.pe + s2 + var * R.Nq;
+      double acc = 0.0;
+      for (int a1 = 0; a1 <= p; ++a1) acc = fma(R.psi1[a1 * n + c1], y[(a1 * n + c2) * n + c3], acc);
+      t.base[e * t.pe + out + var * R.Nq + v] = acc;
+    }
+    __syncthreads();
+  }
+}
+
+// out = V^T in (nodal -> modal) with scratch s1, s2 (nodal-sized).
+template <int D>
+__device__ void apply_VT(const DevRef& R, const Tile& t, int in, int s1, int s2, int out, int nc) {
+  const int n = R.n, p = R.p;
+  if (D == 2) {
+    int rows = (p + 1) * n, tot = t.E * nc * rows;
+    for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+      int row = idx % rows, ev = idx / rows, var = ev % nc, e = ev / nc;
+      int a1 = row / n, c2 = row % n;
+      const double* x = t.base + e * t.pe + in + var * R.Nq;
+      double acc = 0.0;
+      for (int c1 = 0; c1 < n; ++c1) acc = fma(R.psi1[a1 * n + c1], x[c1 + n * c2], acc);
+      t.base[e * t.pe + s1 + var * R.Nq + row] = acc;
+    }
+    __syncthreads();
+    rows = R.Np;
+    tot = t.E * nc * rows;
+    for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+      int m = idx % rows, ev = idx / rows, var = ev % nc, e = ev / nc;
+      int a1 = R.mode[m];
+      const double* y = t.base + e * t.pe + s1 + var * R.Nq;
+      double acc = 0.0;
+      for (int c2 = 0; c2 < n; ++c2) acc = fma(R.psi2[m * n + c2], y[a1 * n + c2], acc);
+      t.base[e * t.pe + out + var * R.Np + m] = acc;
+    }
+    __syncthreads();
+  } else {
+    int rows = (p + 1) * n * n, tot = t.E * nc * rows;
+    for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+      int row = idx % rows, ev = idx / rows, var = ev % nc, e = ev / nc;
+      int c3 = row % n, c2 = (row / n) % n, a1 = row / (n * n);
+      const double* x = t.base + e * t.pe + in + var * R.Nq;
+      double acc = 0.0;
+      for (int c1 = 0; c1 < n; ++c1) acc = fma(R.psi1[a1 * n + c1], x[c1 + n * (c2 + n * c3)], acc);
+      t.base[e * t.pe + s1 + var * R.Nq + row] = acc;
+    }
+    __syncthreads();
+    rows = R.S12 * n;
+    tot = t.E * nc * rows;
+    for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+      int row = idx % rows, ev = idx / rows, var = ev % nc, e = ev / nc;
+      int s = row / n, c3 = row % n, a1 = R.s12a1[s];
+      const double* y = t.base + e * t.pe + s1 + var * R.Nq;
+      double acc = 0.0;
+      for (int c2 = 0; c2 < n; ++c2) acc = fma(R.psi2[s * n + c2], y[(a1 * n + c2) * n + c3], acc);
+      t.base[e * t.pe + s2 + var * R.Nq + row] = acc;
+    }
+    __syncthreads();
+    rows = R.Np;
+    tot = t.E * nc * rows;
+    for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+      int m = idx % rows, ev = idx / rows, var = ev % nc, e = ev / nc;
+      int s = R.mode[m];
+      const double* y = t.base + e * t.pe + s2 + var * R.Nq;
+      double acc = 0.0;
+      for (int c3 = 0; c3 < n; ++c3) acc = fma(R.psi3[m * n + c3], y[s * n + c3], acc);
+      t.base[e * t.pe + out + var * R.Np + m] = acc;
+    }
+    __syncthreads();
+  }
+}
+
+// facet values wf = R^(zeta) w (Eq. (r_2d), Eq. (r_3d)); `y` is nodal scratch (tetrahedra).
+template <int D>
+__device__ void apply_R(const DevRef& R, const Tile& t, int in, int y, int out, int nc) {
+  const int n = R.n;
+  if (D == 3) {
+    int rows = n * n, tot = t.E * nc * rows;
+    for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {  // face 4: extrapolate eta3 -> -1
+      int row = idx % rows, ev = idx / rows, var = ev % nc, e = ev / nc;
+      const double* w = t.base + e * t.pe + in + var * R.Nq;
+      double acc = 0.0;
+      for (int c3 = 0; c3 < n; ++c3) acc = fma(R.l3m[c3], w[row + n * n * c3], acc);
+      t.base[e * t.pe + y + var * R.Nq + row] = acc;
+    }
+    __syncthreads();
+  }
+  int tot = t.E * nc * R.Nfn;
+  for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+    int f = idx % R.Nfn, ev = idx / R.Nfn, var = ev % nc, e = ev / nc;
+    int z = f / R.Nqf, j = f % R.Nqf;
+    const double* w = t.base + e * t.pe + in + var * R.Nq;
+    double acc = 0.0;
+    if (D == 2) {
+      if (z == 0)
+        for (int b = 0; b < n; ++b) acc = fma(R.l2m[b], w[j + n * b], acc);
+      else {
+        const double* l = z == 1 ? R.l1p : R.l1m;
+        for (int a = 0; a < n; ++a) acc = fma(l[a], w[a + n * j], acc);
+      }
+    } else {
+      int a = j % n, b = j / n;
+      if (z == 0) {
+        for (int c2 = 0; c2 < n; ++c2) acc = fma(R.l2m[c2], w[a + n * (c2 + n * b)], acc);
+      } else if (z < 3) {
+        const double* l = z == 1 ? R.l1p : R.l1m;
+        for (int c1 = 0; c1 < n; ++c1) acc = fma(l[c1], w[c1 + n * j], acc);
+      } else {
+        const double* yy = t.base + e * t.pe + y + var * R.Nq;
+        for (int c2 = 0; c2 < n; ++c2) acc = fma(R.L2J[b * n + c2], yy[a + n * c2], acc);
+      }
+    }
+    t.base[e * t.pe + out + var * R.Nfn + f] = acc;
+  }
+  __syncthreads();
+}
+
+// out = V^T (W/J) V in (modal -> modal), the weight-adjusted inverse of
+// Eq. (weight_adjusted_inverse) with M = I: the stored symmetric per-element matrix when
+// R.dense_minv, else sum-factorised through nodal scratch s1, s2, s3.  `out` must differ
+// from `in`, s1 and s2; it may equal s3.
+template <int D>
+__device__ void apply_minv(const DevRef& R, const DevMesh& M, const Tile& t, int64_t e0, int in, int s1, int s2,
+                           int s3, int out, int nc) {
+  const int Np = R.Np, Nq = R.Nq;
+  if (R.dense_minv) {
+    const int tot = t.E * nc * Np;
+    for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+      const int i = idx % Np, ev = idx / Np, var = ev % nc, e = ev / nc;
+      const double* Mi = M.minv + (e0 + e) * (int64_t)Np * Np + i;   // column i == row i (symmetric)
+      const double* x = t.base + e * t.pe + in + var * Np;
+      double acc = 0.0;
+      for (int j = 0; j < Np; ++j) acc = fma(Mi[(int64_t)j * Np], x[j], acc);
+      t.base[e * t.pe + out + var * Np + i] = acc;
+    }
+    __syncthreads();
+    return;
+  }
+  apply_V<D>(R, t, in, s1, s2, s3, nc);
+  for (int idx = threadIdx.x; idx < t.E * nc * Nq; idx += blockDim.x) {
+    const int e = idx / (nc * Nq), v = idx % Nq;
+    t.base[e * t.pe + s3 + idx % (nc * Nq)] *= M.wdj[(e0 + e) * Nq + v];
+  }
+  __syncthreads();
+  apply_VT<D>(R, t, s3, s1, s2, out, nc);
+}
+
+// ---------------------------------------------------------------------------
+// Pointwise maps
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool finite_pos(double x) { return x > 0.0 && x < 1.0e300; }
+
+// entropy variables W(u) = grad_U S (Section 7.1), times the weight W J
+template <int D>
+__device__ __forceinline__ void entropy_vars(const double* u, double gamma, double scale, double* w, int* bad) {
+  double rho = u[0];
+  double ir = 1.0 / rho, vv = 0.0, v[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    v[k] = u[1 + k] * ir;
+    vv = fma(v[k], v[k], vv);
+  }
+  double p = (gamma - 1.0) * (u[D + 1] - 0.5 * rho * vv);
+  if (!finite_pos(rho) || !finite_pos(p)) *bad = 1;
+  double s = log(p) - gamma * log(rho);
+  double b = rho / p;
+  w[0] = scale * ((gamma - s) / (gamma - 1.0) - 0.5 * b * vv);
+#pragma unroll
+  for (int k = 0; k < D; ++k) w[1 + k] = scale * b * v[k];
+  w[D + 1] = -scale * b;
+}
+
+// conservative variables U(w) (inverse of the entropy-variable map) returned as the
+// flux state: b = -w_last = rho/p, v = w_v/b, s = gamma - (gamma-1)(w_1 + b|v|^2/2),
+// ln rho = -(s + ln b)/(gamma-1), p = rho/b.
+template <int D>
+__device__ __forceinline__ NodeState<D> state_from_entropy(const double* w, double gamma, int* bad) {
+  NodeState<D> st;
+  double b = -w[D + 1];
+  if (!finite_pos(b)) *bad = 1;
+  double ib = 1.0 / b, vv = 0.0;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    st.v[k] = w[1 + k] * ib;
+    vv = fma(st.v[k], st.v[k], vv);
+  }
+  double s = gamma - (gamma - 1.0) * (w[0] + 0.5 * b * vv);
+  double lb = log(b);
+  st.lrho = -(s + lb) / (gamma - 1.0);
+  st.rho = exp(st.lrho);
+  st.p = st.rho * ib;
+  st.beta = b;
+  st.lbeta = lb;
+  if (!finite_pos(st.rho) || !finite_pos(st.p)) *bad = 1;
+  return st;
+}
+
+template <int D>
+__device__ __forceinline__ void store_state(double* S, int stride, int idx, const NodeState<D>& s) {
+  S[idx] = s.rho;
+#pragma unroll
+  for (int k = 0; k < D; ++k) S[(1 + k) * stride + idx] = s.v[k];
+  S[(D + 1) * stride + idx] = s.p;
+  S[(D + 2) * stride + idx] = s.beta;
+  S[(D + 3) * stride + idx] = s.lrho;
+  S[(D + 4) * stride + idx] = s.lbeta;
+}
+
+// ---------------------------------------------------------------------------
+// Projection kernel
+// shared layout per element (doubles): M[nc*Np] | A[nc*Nq] | B[nc*Nq] | C[nc*Nq] | F[nc*Nfn]
+// ---------------------------------------------------------------------------
+template <int D>
+__device__ void project_tile(const DevRef& R, const DevMesh& M, int64_t e0, int E, const double* __restrict__ u,
+                             double* __restrict__ w_modal) {
+  extern __shared__ double sm[];
+  constexpr int NC = D + 2, NF = D + 5;
+  const int Np = R.Np, Nq = R.Nq, Nfn = R.Nfn, Ntot = R.Ntot;
+  const int oM = 0, oA = NC * Np, oB = oA + NC * Nq, oC = oB + NC * Nq, oF = oC + NC * Nq;
+  const int pe = oF + NC * Nfn;
+  Tile t{sm, pe, E};
+  // 1. load u~
+  for (int idx = threadIdx.x; idx < E * NC * Np; idx += blockDim.x) {
+    int e = idx / (NC * Np), r = idx % (NC * Np);
+    sm[e * pe + oM + r] = u[(e0 + e) * NC * Np + r];
+  }
+  __syncthreads();
+  // 2. u = V u~
+  apply_V<D>(R, t, oM, oB, oC, oA, NC);
+  // 3. W J W(u)
+  int lbad = 0;
+  for (int idx = threadIdx.x; idx < E * Nq; idx += blockDim.x) {
+    int e = idx / Nq, v = idx % Nq;
+    double uu[NC], ww[NC];
+    double* A = sm + e * pe + oA;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) uu[c] = A[c * Nq + v];
+    entropy_vars<D>(uu, M.gamma, M.wj[(e0 + e) * Nq + v], ww, &lbad);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) A[c * Nq + v] = ww[c];
+  }
+  __syncthreads();
+  // 4-6. w~ = [V^T (W/J) V] V^T (W J W)
+  apply_VT<D>(R, t, oA, oB, oC, oM, NC);
+  apply_minv<D>(R, M, t, e0, oM, oB, oC, oA, oA, NC);
+  for (int idx = threadIdx.x; idx < E * NC * Np; idx += blockDim.x) {
+    int e = idx / (NC * Np);
+    sm[e * pe + oM + idx % (NC * Np)] = sm[e * pe + oA + idx % (NC * Np)];
+  }
+  __syncthreads();
+  if (w_modal) {
+    for (int idx = threadIdx.x; idx < E * NC * Np; idx += blockDim.x) {
+      int e = idx / (NC * Np), r = idx % (NC * Np);
+      w_modal[(e0 + e) * NC * Np + r] = sm[e * pe + oM + r];
+    }
+    if (lbad) atomicOr(M.flag, 1);
+    return;
+  }
+  // 7-8. w = V w~, facet values R w
+  apply_V<D>(R, t, oM, oB, oC, oA, NC);
+  apply_R<D>(R, t, oA, oB, oF, NC);
+  // 9. entropy-projected conservative states at volume and facet nodes
+  for (int idx = threadIdx.x; idx < E * Ntot; idx += blockDim.x) {
+    int e = idx / Ntot, k = idx % Ntot;
+    double ww[NC];
+    const double* src = k < Nq ? sm + e * pe + oA + k : sm + e * pe + oF + (k - Nq);
+    const int str = k < Nq ? Nq : Nfn;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) ww[c] = src[c * str];
+    NodeState<D> st = state_from_entropy<D>(ww, M.gamma, &lbad);
+    store_state<D>(M.states + (e0 + e) * NF * Ntot, Ntot, k, st);
+    if (k >= Nq) M.cfac[(e0 + e) * Nfn + (k - Nq)] = sqrt(M.gamma * st.p / st.rho);
+  }
+  if (lbad) atomicOr(M.flag, 1);
+}
+
+// ---------------------------------------------------------------------------
+// Residual kernel
+// shared layout per element (doubles):
+//   region0 : states Sv[NF*Nq] | Sf[NF*Nfn] | part[NC*n^3] (tets)  -- reused as scratch later
+//   r[NC*Nq] | h[NC*Nfn]
+// ---------------------------------------------------------------------------
+struct ResLayout {
+  int oSv, oSf, oPart, oS1, oS2, oMod, oR, oH, pe;
+};
+
+template <int D>
+__host__ __device__ inline ResLayout res_layout(int Nq, int Nfn, int Np, int n) {
+  constexpr int NC = D + 2, NF = D + 5;
+  ResLayout L;
+  L.oSv = 0;
+  L.oSf = NF * Nq;
+  L.oPart = L.oSf + NF * Nfn;
+  int r0 = L.oPart + (D == 3 ? NC * n * n * n : 0);
+  L.oS1 = 0;
+  L.oS2 = NC * Nq;
+  L.oMod = 2 * NC * Nq;
+  int r0b = L.oMod + NC * Np;
+  if (r0b > r0) r0 = r0b;
+  L.oR = r0;
+  L.oH = L.oR + NC * Nq;
+  L.pe = L.oH + NC * Nfn;
+  return L;
+}
+
+// the tables hold n/2; the adjoint works with the full direction
+template <int D>
+__device__ __forceinline__ void load_dir(const double* base, int slot, int T, int t, double* n) {
+#pragma unroll
+  for (int k = 0; k < D; ++k) n[k] = 2.0 * base[(slot * D + k) * T + t];
+}
+
+// Pair work of one line task (Section 5.1, along collapsed-coordinate lines, Remark 4).
+// Task t of phase ph owns one eta_{ph+1}-line of N nodes and the facet nodes attached to
+// it; accumulators live in registers and the unrolled pairs are independent.
+//   tetrahedra: phase 0 = eta1-lines + facets 2, 3; phase 1 = eta2-lines + facet 1;
+//               phase 2 = eta3-lines + facet-4 pairs (per-task partial sums);
+//   triangles:  phase 0 = eta1-lines + facets 2, 3; phase 1 = eta2-lines + facet 1.
+template <int D, int N>
+__device__ __forceinline__ void line_task(int ph, int t, const DevRef& R, const double* __restrict__ Sv,
+                                          const double* __restrict__ Sf, double* r, double* h, double* part,
+                                          const double* __restrict__ vdir, const double* __restrict__ fdir,
+                                          const FluxK& K) {
+  constexpr int NC = D + 2;
+  const int Nq = R.Nq, Nfn = R.Nfn, Nqf = R.Nqf, T = R.T;
+  int base, stride;
+  if (D == 2) {
+    base = ph == 0 ? N * t : t;
+    stride = ph == 0 ? 1 : N;
+  } else {
+    if (ph == 0) { base = N * t; stride = 1; }
+    else if (ph == 1) { base = (t % N) + N * N * (t / N); stride = N; }
+    else { base = t; stride = N * N; }
+  }
+  double acc[N][NC];
+#pragma unroll
+  for (int a = 0; a < N; ++a)
+#pragma unroll
+    for (int c = 0; c < NC; ++c) acc[a][c] = 0.0;
+  constexpr int Lv = N * (N - 1) / 2;
+  const double* vd = vdir + (size_t)ph * Lv * D * T + t;
+#pragma unroll
+  for (int a = 0, m = 0; a < N; ++a) {
+#pragma unroll
+    for (int b = a + 1; b < N; ++b, ++m) {
+      const NodeState<D> Si = load_state<D>(Sv, Nq, base + a * stride);
+      const NodeState<D> Sj = load_state<D>(Sv, Nq, base + b * stride);
+      double nh[D], F[NC];
+#pragma unroll
+      for (int k = 0; k < D; ++k) nh[k] = vd[(m * D + k) * T];
+      ec_flux_fast<D>(Si, Sj, nh, K, F);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        acc[a][c] -= F[c];
+        acc[b][c] += F[c];
+      }
+    }
+  }
+  if (ph == 0) {
+#pragma unroll
+    for (int zz = 0; zz < 2; ++zz) {
+      const int f = (1 + zz) * Nqf + t;
+      const double* fd = fdir + R.fph_off[0] + (size_t)zz * N * D * T + t;
+      const NodeState<D> Sj = load_state<D>(Sf, Nfn, f);
+      double hs[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) hs[c] = 0.0;
+#pragma unroll
+      for (int a = 0; a < N; ++a) {
+        const NodeState<D> Si = load_state<D>(Sv, Nq, base + a * stride);
+        double nh[D], F[NC];
+#pragma unroll
+        for (int k = 0; k < D; ++k) nh[k] = fd[(a * D + k) * T];
+        ec_flux_fast<D>(Si, Sj, nh, K, F);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          acc[a][c] -= F[c];
+          hs[c] += F[c];
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < NC; ++c) h[c * Nfn + f] -= hs[c];
+    }
+  } else if (ph == 1) {
+    const int f = t;
+    const double* fd = fdir + R.fph_off[1] + t;
+    const NodeState<D> Sj = load_state<D>(Sf, Nfn, f);
+    double hs[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) hs[c] = 0.0;
+#pragma unroll
+    for (int a = 0; a < N; ++a) {
+      const NodeState<D> Si = load_state<D>(Sv, Nq, base + a * stride);
+      double nh[D], F[NC];
+#pragma unroll
+      for (int k = 0; k < D; ++k) nh[k] = fd[(a * D + k) * T];
+      ec_flux_fast<D>(Si, Sj, nh, K, F);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        acc[a][c] -= F[c];
+        hs[c] += F[c];
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) h[c * Nfn + f] -= hs[c];
+  } else if (D == 3) {
+    // facet 4: nodes (a1, b') with a1 = t % N, against the eta3-line (a1, a2 = t / N)
+    const double* fd = fdir + R.fph_off[3] + t;
+    const int a1 = t % N;
+#pragma unroll 1
+    for (int bp = 0; bp < N; ++bp) {
+      const int f = 3 * Nqf + a1 + N * bp;
+      const NodeState<D> Sj = load_state<D>(Sf, Nfn, f);
+      double hs[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) hs[c] = 0.0;
+#pragma unroll
+      for (int a = 0; a < N; ++a) {
+        const NodeState<D> Si = load_state<D>(Sv, Nq, base + a * stride);
+        double nh[D], F[NC];
+#pragma unroll
+        for (int k = 0; k < D; ++k) nh[k] = fd[((bp * N + a) * D + k) * T];
+        ec_flux_fast<D>(Si, Sj, nh, K, F);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          acc[a][c] -= F[c];
+          hs[c] += F[c];
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < NC; ++c) part[(c * T + t) * N + bp] = hs[c];
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < N; ++a)
+#pragma unroll
+    for (int c = 0; c < NC; ++c) r[c * Nq + base + a * stride] += acc[a][c];
+}
+
+template <int D, int N>
+__device__ void residual_tile(const DevRef& R, const DevMesh& M, int64_t e0, int E, const Epilogue& ep) {
+  extern __shared__ double sm[];
+  constexpr int NC = D + 2, NF = D + 5;
+  const int n = R.n, Nq = R.Nq, Nfn = R.Nfn, Ntot = R.Ntot, Np = R.Np, T = R.T, Nqf = R.Nqf;
+  const ResLayout Ly = res_layout<D>(Nq, Nfn, Np, n);
+  const int pe = Ly.pe;
+  const double inv_gm1 = 1.0 / (M.gamma - 1.0);
+  Tile tile{sm, pe, E};
+
+  // 1. load states
+  for (int idx = threadIdx.x; idx < E * NF * Ntot; idx += blockDim.x) {
+    int e = idx / (NF * Ntot), r = idx % (NF * Ntot), f = r / Ntot, k = r % Ntot;
+    double val = M.states[(e0 + e) * NF * Ntot + r];
+    if (k < Nq)
+      sm[e * pe + Ly.oSv + f * Nq + k] = val;
+    else
+      sm[e * pe + Ly.oSf + f * Nfn + (k - Nq)] = val;
+  }
+  for (int idx = threadIdx.x; idx < E * NC * Nq; idx += blockDim.x) {
+    int e = idx / (NC * Nq);
+    sm[e * pe + Ly.oR + idx % (NC * Nq)] = 0.0;
+  }
+  __syncthreads();
+  // 2. interface flux h = B J f* (Eq. (interface_flux), Eq. (num_flux), Eq. (wave_speed))
+  for (int idx = threadIdx.x; idx < E * Nfn; idx += blockDim.x) {
+    int e = idx / Nfn, f = idx % Nfn;
+    const int64_t eg = e0 + e;
+    NodeState<D> L = load_state<D>(sm + e * pe + Ly.oSf, Nfn, f);
+    const int64_t e2 = M.nbr_e[eg * Nfn + f];
+    const int f2 = M.nbr_f[eg * Nfn + f];
+    NodeState<D> Rr = load_state<D>(M.states + e2 * NF * Ntot + Nq, Ntot, f2);
+    double nn[D], nh[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      nn[k] = M.nrm[(eg * D + k) * Nfn + f];
+      nh[k] = 0.5 * nn[k];
+    }
+    double F[NC];
+    ec_flux_fast<D>(L, Rr, nh, make_fluxk(M.gamma), F);
+    if (M.lf) {
+      double vnL = 0.0, vnR = 0.0, vvL = 0.0, vvR = 0.0;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        vnL = fma(L.v[k], nn[k], vnL);
+        vnR = fma(Rr.v[k], nn[k], vnR);
+        vvL = fma(L.v[k], L.v[k], vvL);
+        vvR = fma(Rr.v[k], Rr.v[k], vvR);
+      }
+      double lam = fmax(fabs(vnL), fabs(vnR)) + fmax(M.cfac[eg * Nfn + f], M.cfac[e2 * Nfn + f2]);
+      double hl = 0.5 * lam;
+      F[0] -= hl * (Rr.rho - L.rho);
+#pragma unroll
+      for (int k = 0; k < D; ++k) F[1 + k] -= hl * (Rr.rho * Rr.v[k] - L.rho * L.v[k]);
+      double EL = L.p * inv_gm1 + 0.5 * L.rho * vvL, ER = Rr.p * inv_gm1 + 0.5 * Rr.rho * vvR;
+      F[D + 1] -= hl * (ER - EL);
+    }
+    const double bj = M.bj[eg * Nfn + f];
+    double* h = sm + e * pe + Ly.oH;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) h[c * Nfn + f] = bj * F[c];
+  }
+  __syncthreads();
+  // 3. line-based flux differencing and facet correction
+  {
+    const FluxK K = make_fluxk(M.gamma);
+    const int tid = threadIdx.x;
+    const int el = tid / T, t = tid % T;
+    const bool active = el < E;
+    const int64_t eg = e0 + el;
+    const double* vdir = active ? M.vdir + eg * (int64_t)R.nvp * D : nullptr;
+    const double* fdir = active ? M.fdir + eg * (int64_t)R.nfp * D : nullptr;
+    for (int ph = 0; ph < D; ++ph) {
+      if (active)
+        line_task<D, N>(ph, t, R, sm + el * pe + Ly.oSv, sm + el * pe + Ly.oSf, sm + el * pe + Ly.oR,
+                        sm + el * pe + Ly.oH, sm + el * pe + Ly.oPart, vdir, fdir, K);
+      __syncthreads();
+    }
+  }
+  if (D == 3) {
+    for (int idx = threadIdx.x; idx < E * NC * Nqf; idx += blockDim.x) {
+      int e = idx / (NC * Nqf), rr = idx % (NC * Nqf), c = rr / Nqf, j = rr % Nqf;
+      int a = j % n, bp = j / n;
+      const double* pp = sm + e * pe + Ly.oPart + c * T * n;
+      double s = 0.0;
+      for (int b2 = 0; b2 < n; ++b2) s += pp[(a + n * b2) * n + bp];
+      sm[e * pe + Ly.oH + c * Nfn + 3 * Nqf + j] -= s;
+    }
+    __syncthreads();
+  }
+  // 4. lift: r -= sum_zeta R^T h  (h = B J f* - C^T 1)
+  if (D == 3) {
+    // y[a + n*b2] = sum_b' L2J[b'][b2] h4[a + n*b']  (into scratch part region, free now)
+    for (int idx = threadIdx.x; idx < E * NC * n * n; idx += blockDim.x) {
+      int e = idx / (NC * n * n), rr = idx % (NC * n * n), c = rr / (n * n), ab = rr % (n * n);
+      int a = ab % n, b2 = ab / n;
+      const double* hh = sm + e * pe + Ly.oH + c * Nfn + 3 * Nqf;
+      double s = 0.0;
+      for (int bp = 0; bp < n; ++bp) s = fma(R.L2J[bp * n + b2], hh[a + n * bp], s);
+      sm[e * pe + Ly.oPart + rr] = s;
+    }
+    __syncthreads();
+  }
+  for (int idx = threadIdx.x; idx < E * NC * Nq; idx += blockDim.x) {
+    int e = idx / (NC * Nq), rr = idx % (NC * Nq), c = rr / Nq, v = rr % Nq;
+    const double* hh = sm + e * pe + Ly.oH + c * Nfn;
+    double s;
+    if (D == 2) {
+      int a = v % n, b = v / n;
+      s = R.l2m[b] * hh[a] + R.l1p[a] * hh[Nqf + b] + R.l1m[a] * hh[2 * Nqf + b];
+    } else {
+      int a = v % n, b = (v / n) % n, c3 = v / (n * n);
+      const double* y = sm + e * pe + Ly.oPart + c * n * n;
+      s = R.l2m[b] * hh[a + n * c3] + R.l1p[a] * hh[Nqf + b + n * c3] + R.l1m[a] * hh[2 * Nqf + b + n * c3] +
+          R.l3m[c3] * y[a + n * b];
+    }
+    sm[e * pe + Ly.oR + rr] -= s;
+  }
+  __syncthreads();
+  if (ep.mode == 2) {
+    // diagnostics: per element sum_i r_i (per variable), sum w.r, sum |w r|
+    for (int e = threadIdx.x / 32; e < E; e += blockDim.x / 32) {
+      const int lane = threadIdx.x % 32;
+      double acc[NC + 2];
+#pragma unroll
+      for (int c = 0; c < NC + 2; ++c) acc[c] = 0.0;
+      for (int v = lane; v < Nq; v += 32) {
+        NodeState<D> s = load_state<D>(sm + e * pe + Ly.oSv, Nq, v);
+        double vv = 0.0;
+#pragma unroll
+        for (int k = 0; k < D; ++k) vv += s.v[k] * s.v[k];
+        double sent = (1.0 - M.gamma) * s.lrho - s.lbeta;   // ln(p / rho^gamma)
+        double w[NC];
+        w[0] = (M.gamma - sent) * inv_gm1 - 0.5 * s.beta * vv;
+#pragma unroll
+        for (int k = 0; k < D; ++k) w[1 + k] = s.beta * s.v[k];
+        w[D + 1] = -s.beta;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          double rv = sm[e * pe + Ly.oR + c * Nq + v];
+          acc[c] += rv;
+          acc[NC] += w[c] * rv;
+          acc[NC + 1] += fabs(w[c] * rv);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < NC + 2; ++c) {
+        double x = acc[c];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) ep.diag[(e0 + e) * (NC + 2) + c] = x;
+      }
+    }
+    return;
+  }
+  // 5. d u~/dt = [V^T (W/J) V] (V^T r)   (Eq. (matvec_dudt), M = I)
+  apply_VT<D>(R, tile, Ly.oR, Ly.oS1, Ly.oS2, Ly.oMod, NC);
+  apply_minv<D>(R, M, tile, e0, Ly.oMod, Ly.oS1, Ly.oS2, Ly.oR, Ly.oR, NC);
+  for (int idx = threadIdx.x; idx < E * NC * Np; idx += blockDim.x) {   // result to oMod
+    int e = idx / (NC * Np);
+    sm[e * pe + Ly.oMod + idx % (NC * Np)] = sm[e * pe + Ly.oR + idx % (NC * Np)];
+  }
+  __syncthreads();
+  // 6. epilogue
+  for (int idx = threadIdx.x; idx < E * NC * Np; idx += blockDim.x) {
+    int e = idx / (NC * Np), rr = idx % (NC * Np);
+    const int64_t g = (e0 + e) * NC * Np + rr;
+    double k = sm[e * pe + Ly.oMod + rr];
+    if (ep.mode == 0) {
+      ep.dudt[g] = k;
+    } else {
+      double acc = ep.acc_in[g] + ep.cb * k;
+      if (ep.stage_out) ep.stage_out[g] = ep.u0[g] + ep.ca * k;
+      ep.acc_out[g] = acc;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Vector-Jacobian product (reverse mode, hand-derived; not in the paper)
+//
+// Per-node cotangents are carried for the primitive triple q = (rho, v, p); the
+// derived fields beta = rho/p, ln rho, ln beta are functions of q and their
+// cotangents are folded back inside the pair adjoint.
+// ---------------------------------------------------------------------------
+
+// log mean and its partial derivatives, with the same branches as log_mean():
+// series branch, LM = (a+b)/(2F(u)), F = 1 + u/3 + u^2/5 + u^3/7, u = ((b-a)/(a+b))^2:
+//   dLM/da = 1/(2F) + 2 f b F'(u)/((a+b) F^2),  dLM/db = 1/(2F) - 2 f a F'(u)/((a+b) F^2)
+// direct branch, LM = (b-a)/L, L = ln b - ln a:
+//   dLM/da = (LM/a - 1)/L,  dLM/db = (1 - LM/b)/L
+__device__ __forceinline__ void log_mean_grad(double a, double b, double la, double lb, double* lm, double* da,
+                                              double* db) {
+  double s = a + b, d = b - a, f = d / s, u = f * f;
+  if (u < 1.0e-4) {
+    double F = 1.0 + u * (1.0 / 3.0 + u * (1.0 / 5.0 + u * (1.0 / 7.0)));
+    double Fp = 1.0 / 3.0 + u * (2.0 / 5.0 + u * (3.0 / 7.0));
+    *lm = s / (2.0 + u * (2.0 / 3.0 + u * (2.0 / 5.0 + u * (2.0 / 7.0))));
+    double t = 2.0 * f * Fp / (s * F * F);
+    *da = 0.5 / F + t * b;
+    *db = 0.5 / F - t * a;
+  } else {
+    double L = lb - la, m = d / L;
+    *lm = m;
+    *da = (m / a - 1.0) / L;
+    *db = (1.0 - m / b) / L;
+  }
+}
+
+// Adds (d F/d qL)^T Fb to qL and (d F/d qR)^T Fb to qR for the directional flux of ec_flux.
+template <int D>
+__device__ __forceinline__ void ec_flux_adj(const NodeState<D>& L, const NodeState<D>& R, const double* n,
+                                            double inv_gm1, const double* Fb, double* qL, double* qR) {
+  double rl, dra, drb, bl, dba, dbb;
+  log_mean_grad(L.rho, R.rho, L.lrho, R.lrho, &rl, &dra, &drb);
+  log_mean_grad(L.beta, R.beta, L.lbeta, R.lbeta, &bl, &dba, &dbb);
+  const double ib = 1.0 / bl;
+  double vnL = 0.0, vnR = 0.0, vv = 0.0;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    vnL = fma(n[k], L.v[k], vnL);
+    vnR = fma(n[k], R.v[k], vnR);
+    vv = fma(L.v[k], R.v[k], vv);
+  }
+  const double frho = rl * 0.5 * (vnL + vnR);
+  const double FE = Fb[D + 1];
+  double frho_b = Fb[0] + FE * (0.5 * vv + inv_gm1 * ib);
+  double pavg_b = 0.0;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    frho_b = fma(Fb[1 + k], 0.5 * (L.v[k] + R.v[k]), frho_b);
+    pavg_b = fma(Fb[1 + k], n[k], pavg_b);
+  }
+  const double vv_b = 0.5 * FE * frho;
+  const double ib_b = FE * frho * inv_gm1;
+  double pL_b = 0.5 * pavg_b + 0.5 * FE * vnR;
+  double pR_b = 0.5 * pavg_b + 0.5 * FE * vnL;
+  const double rl_b = frho_b * 0.5 * (vnL + vnR);
+  const double vnL_b = 0.5 * FE * R.p + 0.5 * frho_b * rl;
+  const double vnR_b = 0.5 * FE * L.p + 0.5 * frho_b * rl;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    const double vs_b = 0.5 * Fb[1 + k] * frho;
+    qL[1 + k] += vs_b + vv_b * R.v[k] + vnL_b * n[k];
+    qR[1 + k] += vs_b + vv_b * L.v[k] + vnR_b * n[k];
+  }
+  double rhoL_b = rl_b * dra, rhoR_b = rl_b * drb;
+  const double bl_b = -ib * ib * ib_b;
+  const double bL_b = bl_b * dba, bR_b = bl_b * dbb;
+  rhoL_b += bL_b / L.p;
+  pL_b -= bL_b * L.beta / L.p;
+  rhoR_b += bR_b / R.p;
+  pR_b -= bR_b * R.beta / R.p;
+  qL[0] += rhoL_b;
+  qR[0] += rhoR_b;
+  qL[D + 1] += pL_b;
+  qR[D + 1] += pR_b;
+}
+
+// adjoint of the interface flux f* = f#(q-, q+, n) - lambda/2 (U+ - U-) (Eq. (num_flux),
+// Eq. (wave_speed)); max/|.| use the sub-gradient with ties to the interior side.
+template <int D>
+__device__ __forceinline__ void iface_adj(const NodeState<D>& L, const NodeState<D>& R, const double* n,
+                                          double inv_gm1, double cL, double cR, int lf, const double* fb,
+                                          double* qL, double* qR) {
+  ec_flux_adj<D>(L, R, n, inv_gm1, fb, qL, qR);
+  if (!lf) return;
+  constexpr int NC = D + 2;
+  double vnL = 0.0, vnR = 0.0, vvL = 0.0, vvR = 0.0;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    vnL = fma(L.v[k], n[k], vnL);
+    vnR = fma(R.v[k], n[k], vnR);
+    vvL = fma(L.v[k], L.v[k], vvL);
+    vvR = fma(R.v[k], R.v[k], vvR);
+  }
+  const double lam = fmax(fabs(vnL), fabs(vnR)) + fmax(cL, cR);
+  double UL[NC], UR[NC];
+  UL[0] = L.rho;
+  UR[0] = R.rho;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    UL[1 + k] = L.rho * L.v[k];
+    UR[1 + k] = R.rho * R.v[k];
+  }
+  UL[D + 1] = L.p * inv_gm1 + 0.5 * L.rho * vvL;
+  UR[D + 1] = R.p * inv_gm1 + 0.5 * R.rho * vvR;
+  double lam_b = 0.0;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) lam_b -= 0.5 * fb[c] * (UR[c] - UL[c]);
+  // U(q) adjoints with U+_b = -lam/2 fb, U-_b = +lam/2 fb
+  const double hl = 0.5 * lam;
+  {
+    double ER = -hl * fb[D + 1], EL = hl * fb[D + 1];
+    qR[0] += -hl * fb[0] + 0.5 * vvR * ER;
+    qL[0] += hl * fb[0] + 0.5 * vvL * EL;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      qR[0] += -hl * fb[1 + k] * R.v[k];
+      qL[0] += hl * fb[1 + k] * L.v[k];
+      qR[1 + k] += -hl * fb[1 + k] * R.rho + ER * R.rho * R.v[k];
+      qL[1 + k] += hl * fb[1 + k] * L.rho + EL * L.rho * L.v[k];
+    }
+    qR[D + 1] += ER * inv_gm1;
+    qL[D + 1] += EL * inv_gm1;
+  }
+  if (fabs(vnL) >= fabs(vnR)) {
+    const double g = lam_b * (vnL > 0.0 ? 1.0 : (vnL < 0.0 ? -1.0 : 0.0));
+#pragma unroll
+    for (int k = 0; k < D; ++k) qL[1 + k] += g * n[k];
+  } else {
+    const double g = lam_b * (vnR > 0.0 ? 1.0 : (vnR < 0.0 ? -1.0 : 0.0));
+#pragma unroll
+    for (int k = 0; k < D; ++k) qR[1 + k] += g * n[k];
+  }
+  if (cL >= cR) {
+    qL[D + 1] += lam_b * cL / (2.0 * L.p);
+    qL[0] -= lam_b * cL / (2.0 * L.rho);
+  } else {
+    qR[D + 1] += lam_b * cR / (2.0 * R.p);
+    qR[0] -= lam_b * cR / (2.0 * R.rho);
+  }
+}
+
+// (dq/dw)^T qb for q = (rho, v, p) = U(w) written through the entropy variables:
+// b = -w_last, v = w_v/b, ln rho = -(s + ln b)/(gamma-1), s = gamma - (gamma-1)(w_1 + b|v|^2/2), p = rho/b.
+template <int D>
+__device__ __forceinline__ void qbar_to_wbar(const NodeState<D>& s, const double* qb, double gamma, double* wb) {
+  double vv = 0.0;
+#pragma unroll
+  for (int k = 0; k < D; ++k) vv = fma(s.v[k], s.v[k], vv);
+  const double b = s.beta;
+  const double Lb = qb[0] * s.rho + qb[D + 1] * s.p;   // cotangent of ln rho
+  double bb = -qb[D + 1] * s.p / b + Lb * (-0.5 * vv - 1.0 / ((gamma - 1.0) * b));
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    bb -= qb[1 + k] * s.v[k] / b;
+    wb[1 + k] = Lb * s.v[k] + qb[1 + k] / b;
+  }
+  wb[0] = Lb;
+  wb[D + 1] = -bb;
+}
+
+// (d W/du)^T g for the entropy variables of the conservative state u (Section 7.1).
+template <int D>
+__device__ __forceinline__ void entropy_vars_adj(const double* u, double gamma, const double* g, double* ub) {
+  const double rho = u[0];
+  double v[D], vv = 0.0;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    v[k] = u[1 + k] / rho;
+    vv = fma(v[k], v[k], vv);
+  }
+  const double p = (gamma - 1.0) * (u[D + 1] - 0.5 * rho * vv);
+  const double b = rho / p;
+  double bb = -g[D + 1] - 0.5 * vv * g[0];
+  double vb[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    bb += g[1 + k] * v[k];
+    vb[k] = g[1 + k] * b - g[0] * b * v[k];
+  }
+  const double sb = -g[0] / (gamma - 1.0);
+  const double pb = sb / p - bb * b / p;
+  const double rb = -sb * gamma / rho + bb / p;
+  ub[D + 1] = pb * (gamma - 1.0);
+  double r = rb + pb * (gamma - 1.0) * 0.5 * vv;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    ub[1 + k] = vb[k] / rho - pb * (gamma - 1.0) * v[k];
+    r -= vb[k] * v[k] / rho;
+  }
+  ub[0] = r;
+}
+
+// out (nodal, += sign * R^T in) with scratch y (tetrahedra)
+template <int D>
+__device__ void apply_RT(const DevRef& R, const Tile& t, int in, int y, int out, int nc, double sign) {
+  const int n = R.n, Nq = R.Nq, Nfn = R.Nfn, Nqf = R.Nqf;
+  if (D == 3) {
+    for (int idx = threadIdx.x; idx < t.E * nc * n * n; idx += blockDim.x) {
+      int e = idx / (nc * n * n), rr = idx % (nc * n * n), c = rr / (n * n), ab = rr % (n * n);
+      int a = ab % n, b2 = ab / n;
+      const double* hh = t.base + e * t.pe + in + c * Nfn + 3 * Nqf;
+      double s = 0.0;
+      for (int bp = 0; bp < n; ++bp) s = fma(R.L2J[bp * n + b2], hh[a + n * bp], s);
+      t.base[e * t.pe + y + rr] = s;
+    }
+    __syncthreads();
+  }
+  for (int idx = threadIdx.x; idx < t.E * nc * Nq; idx += blockDim.x) {
+    int e = idx / (nc * Nq), rr = idx % (nc * Nq), c = rr / Nq, v = rr % Nq;
+    const double* hh = t.base + e * t.pe + in + c * Nfn;
+    double s;
+    if (D == 2) {
+      int a = v % n, b = v / n;
+      s = R.l2m[b] * hh[a] + R.l1p[a] * hh[Nqf + b] + R.l1m[a] * hh[2 * Nqf + b];
+    } else {
+      int a = v % n, b = (v / n) % n, c3 = v / (n * n);
+      const double* yy = t.base + e * t.pe + y + c * n * n;
+      s = R.l2m[b] * hh[a + n * c3] + R.l1p[a] * hh[Nqf + b + n * c3] + R.l1m[a] * hh[2 * Nqf + b + n * c3] +
+          R.l3m[c3] * yy[a + n * b];
+    }
+    t.base[e * t.pe + out + rr] += sign * s;
+  }
+  __syncthreads();
+}
+
+// Residual adjoint: cot (cotangent of d u~/dt) -> per-node cotangents of q at own volume
+// and facet nodes (qbar [E][NQ][Ntot]) and, per facet node, the cotangent of the
+// neighbour's state through this element's interface flux (qext [E][NQ][Nfn]).
+struct AdjLayout {
+  int oReg, oM, oS1, oS2, oSv, oSf, oRb, oHb, oQv, oQf, oPart, pe;
+};
+
+template <int D>
+__host__ __device__ inline AdjLayout adj_layout(int Nq, int Nfn, int Np, int n) {
+  constexpr int NC = D + 2, NF = D + 5, NQ = D + 2;
+  AdjLayout L;
+  L.oReg = 0;
+  L.oS1 = 0;
+  L.oS2 = NC * Nq;
+  L.oM = 2 * NC * Nq;
+  L.oSv = 0;
+  L.oSf = NF * Nq;
+  int r0 = 2 * NC * Nq + NC * Np;
+  if (NF * (Nq + Nfn) > r0) r0 = NF * (Nq + Nfn);
+  L.oRb = r0;
+  L.oHb = L.oRb + NC * Nq;
+  L.oQv = L.oHb + NC * Nfn;
+  L.oQf = L.oQv + NQ * Nq;
+  L.oPart = L.oQf + NQ * Nfn;
+  L.pe = L.oPart + (D == 3 ? NQ * n * n * n : 0);
+  return L;
+}
+
+}  // namespace esd

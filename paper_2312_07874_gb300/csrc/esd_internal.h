@@ -44,6 +44,8 @@ struct RefTables {
   std::vector<double> xi_vol, xi_fac; // [Nq*dim], [Nfn*dim]
   std::vector<double> deta;           // [Nq][3][3]: d eta_k / d xi_l at volume nodes (k-major)
   double nhat[4][3] = {};
+  std::vector<double> Vd;             // [Nq][Np] dense generalized Vandermonde (library node order)
+  int dense_minv = 0;                 // apply V^T (W/J) V as a stored per-element Np x Np matrix
 };
 
 // Per-mesh host geometry (setup.cpp) ready to upload.
@@ -55,6 +57,7 @@ struct HostMesh {
   std::vector<double> bj, nrm;        // [E][Nfn], [E][dim][Nfn]
   std::vector<int32_t> nbr_e, nbr_f;  // [E][Nfn]
   std::vector<double> xvol;           // [E][Nq][dim]
+  std::vector<double> minv;           // [E][Np][Np] V^T (W/J) V (when ref.dense_minv)
 };
 
 esd_status build_ref(int dim, int p, RefTables* out, std::string* err);
@@ -68,11 +71,13 @@ struct DevRef {
   const int *off1, *s12a1, *moff, *mode;
   const double *l1m, *l1p, *l2m, *l3m, *L2J;
   const double* wvol;
+  int dense_minv;
 };
 
 struct DevMesh {
   int64_t E;
   const double *vdir, *fdir, *wj, *wdj, *bj, *nrm;
+  const double* minv;   // [E][Np][Np] weight-adjusted inverse (symmetric), or null
   const int32_t *nbr_e, *nbr_f;
   double* states;   // [E][nfields][Ntot]
   double* cfac;     // [E][Nfn] sound speed at facet nodes
@@ -127,8 +132,19 @@ cudaError_t launch_vjp(const DevRef& R, const DevMesh& M, const LaunchCfg& L, co
                        double* grad, double* qbar, double* qext, cudaStream_t s);
 cudaError_t launch_axpby(double* out, double a, const double* x, double b, const double* y, int64_t n,
                          cudaStream_t s);
-cudaError_t launch_batch(int dim, int stage, const BatchMesh* meshes, const BatchItem* items, int nitems,
+cudaError_t launch_batch(int dim, int n, int stage, const BatchMesh* meshes, const BatchItem* items, int nitems,
                          int grid, int threads, size_t smem, cudaStream_t s);
+// per-dimension residual instantiations (residual_d2.cu, residual_d3.cu)
+cudaError_t launch_residual_d2(const DevRef& R, const DevMesh& M, const LaunchCfg& L, const Epilogue& ep,
+                               cudaStream_t s);
+cudaError_t launch_residual_d3(const DevRef& R, const DevMesh& M, const LaunchCfg& L, const Epilogue& ep,
+                               cudaStream_t s);
+cudaError_t launch_residual_batch_d2(int n, const BatchMesh* meshes, const BatchItem* items, int nitems, int grid,
+                                     int threads, size_t smem, cudaStream_t s);
+cudaError_t launch_residual_batch_d3(int n, const BatchMesh* meshes, const BatchItem* items, int nitems, int grid,
+                                     int threads, size_t smem, cudaStream_t s);
+cudaError_t set_residual_smem_d2(int lim);
+cudaError_t set_residual_smem_d3(int lim);
 cudaError_t launch_reduce_diag(const double* part, int64_t E, int ncol, double* out, cudaStream_t s);
 cudaError_t launch_copy(const double* src, double* dst, int64_t n, cudaStream_t s);
 cudaError_t measure_fp64(double* flops, cudaStream_t s);

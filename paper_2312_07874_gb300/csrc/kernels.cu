@@ -18,386 +18,9 @@
 #include <cstdio>
 #include <algorithm>
 
-#include "esd_internal.h"
+#include "device.cuh"
 
 namespace esd {
-
-// ---------------------------------------------------------------------------
-// Per-node state and the two-point flux (Section 7.2)
-// ---------------------------------------------------------------------------
-template <int D>
-struct NodeState {
-  double rho, v[D], p, beta, lrho, lbeta;
-};
-
-// fields are stored SoA: S[field*stride + idx]
-template <int D>
-__device__ __forceinline__ NodeState<D> load_state(const double* S, int stride, int idx) {
-  NodeState<D> s;
-  s.rho = S[idx];
-#pragma unroll
-  for (int k = 0; k < D; ++k) s.v[k] = S[(1 + k) * stride + idx];
-  s.p = S[(D + 1) * stride + idx];
-  s.beta = S[(D + 2) * stride + idx];
-  s.lrho = S[(D + 3) * stride + idx];
-  s.lbeta = S[(D + 4) * stride + idx];
-  return s;
-}
-
-// {{a}}_ln with per-node logarithms: for u = ((b-a)/(b+a))^2 < 1e-4 the series of
-// ln(b/a) = 2 artanh((b-a)/(b+a)) gives (a+b)/(2 + 2u/3 + 2u^2/5 + 2u^3/7);
-// otherwise (b-a)/(ln b - ln a).
-__device__ __forceinline__ double log_mean(double a, double b, double la, double lb) {
-  double s = a + b, d = b - a;
-  double f = d / s, u = f * f;
-  if (u < 1.0e-4) return s / (2.0 + u * (2.0 / 3.0 + u * (2.0 / 5.0 + u * (2.0 / 7.0))));
-  return d / (lb - la);
-}
-
-__device__ __forceinline__ double inv_log_mean(double a, double b, double la, double lb) {
-  double s = a + b, d = b - a;
-  double f = d / s, u = f * f;
-  if (u < 1.0e-4) return (2.0 + u * (2.0 / 3.0 + u * (2.0 / 5.0 + u * (2.0 / 7.0)))) / s;
-  return (lb - la) / d;
-}
-
-// Directional entropy-conservative flux f#(U^-,U^+,n) = sum_m n_m f_m^# (Eq. (ranocha_flux));
-// the energy component uses rho_ln {{v}}.n (v^-.v^+/2 + 1/((gamma-1){{rho/p}}_ln)) + (p^- v^+.n + p^+ v^-.n)/2.
-template <int D>
-__device__ __forceinline__ void ec_flux(const NodeState<D>& L, const NodeState<D>& R, const double* n,
-                                        double inv_gm1, double* F) {
-  double rho_ln = log_mean(L.rho, R.rho, L.lrho, R.lrho);
-  double ib_ln = inv_log_mean(L.beta, R.beta, L.lbeta, R.lbeta);
-  double vnL = 0.0, vnR = 0.0, vv = 0.0;
-#pragma unroll
-  for (int k = 0; k < D; ++k) {
-    vnL = fma(n[k], L.v[k], vnL);
-    vnR = fma(n[k], R.v[k], vnR);
-    vv = fma(L.v[k], R.v[k], vv);
-  }
-  double frho = rho_ln * 0.5 * (vnL + vnR);
-  double pavg = 0.5 * (L.p + R.p);
-  F[0] = frho;
-#pragma unroll
-  for (int k = 0; k < D; ++k) F[1 + k] = fma(frho, 0.5 * (L.v[k] + R.v[k]), pavg * n[k]);
-  F[D + 1] = fma(frho, fma(0.5, vv, inv_gm1 * ib_ln), 0.5 * (L.p * vnR + R.p * vnL));
-}
-
-// ---------------------------------------------------------------------------
-// Sum-factorised PKD transforms (Section 5.2) on a tile of E elements.
-// Buffers are per element with stride `pe` (doubles); each holds N_c variables.
-// ---------------------------------------------------------------------------
-struct Tile {
-  double* base;   // shared memory
-  int pe;         // doubles per element
-  int E;          // elements in this tile
-};
-
-// out = V in  (modal -> nodal), using scratch s1 (and s2 for tetrahedra).  All buffers
-// distinct, except that for tetrahedra `out` may equal s1.
-template <int D>
-__device__ void apply_V(const DevRef& R, const Tile& t, int in, int s1, int s2, int out, int nc) {
-  const int n = R.n, p = R.p;
-  if (D == 2) {
-    int rows = (p + 1) * n, tot = t.E * nc * rows;
-    for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
-      int row = idx % rows, ev = idx / rows, var = ev % nc, e = ev / nc;
-      int a1 = row / n, c2 = row % n;
-      const double* x = t.base + e * t.pe + in + var * R.Np;
-      int m0 = R.off1[a1];
-      double acc = 0.0;
-      for (int a2 = 0; a2 <= p - a1; ++a2) acc = fma(R.psi2[(m0 + a2) * n + c2], x[m0 + a2], acc);
-      t.base[e * t.pe + s1 + var * R.Nq + row] = acc;
-    }
-    __syncthreads();
-    rows = R.Nq;
-    tot = t.E * nc * rows;
-    for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
-      int v = idx % rows, ev = idx / rows, var = ev % nc, e = ev / nc;
-      int c1 = v % n, c2 = v / n;
-      const double* y = t.base + e * t.pe + s1 + var * R.Nq;
-      double acc = 0.0;
-      for (int a1 = 0; a1 <= p; ++a1) acc = fma(R.psi1[a1 * n + c1], y[a1 * n + c2], acc);
-      t.base[e * t.pe + out + var * R.Nq + v] = acc;
-    }
-    __syncthreads();
-  } else {
-    // stage 1: contract alpha3 -> [s12][c3]   (into s1)
-    int rows = R.S12 * n, tot = t.E * nc * rows;
-    for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
-      int row = idx % rows, ev = idx / rows, var = ev % nc, e = ev / nc;
-      int s = row / n, c3 = row % n;
-      int a1 = R.s12a1[s], a2 = s - R.off1[a1], m0 = R.moff[s];
-      const double* x = t.base + e * t.pe + in + var * R.Np;
-      double acc = 0.0;
-      for (int a3 = 0; a3 <= p - a1 - a2; ++a3) acc = fma(R.psi3[(m0 + a3) * n + c3], x[m0 + a3], acc);
-      t.base[e * t.pe + s1 + var * R.Nq + row] = acc;
-    }
-    __syncthreads();
-    // stage 2: contract alpha2 -> [a1][c2][c3]  (into s2)
-    rows = (p + 1) * n * n;
-    tot = t.E * nc * rows;
-    for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
-      int row = idx % rows, ev = idx / rows, var = ev % nc, e = ev / nc;
-      int c3 = row % n, c2 = (row / n) % n, a1 = row / (n * n);
-      const double* y = t.base + e * t.pe + s1 + var * R.Nq;
-      int s0 = R.off1[a1];
-      double acc = 0.0;
-      for (int a2 = 0; a2 <= p - a1; ++a2) acc = fma(R.psi2[(s0 + a2) * n + c2], y[(s0 + a2) * n + c3], acc);
-      t.base[e * t.pe + s2 + var * R.Nq + row] = acc;
-    }
-    __syncthreads();
-    // stage 3: contract alpha1 -> nodal
-    rows = R.Nq;
-    tot = t.E * nc * rows;
-    for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
-      int v = idx % rows, ev = idx / rows, var = ev % nc, e = ev / nc;
-      int c1 = v % n, c2 = (v / n) % n, c3 = v / (n * n);
-      const double* y = t.base + e * t.pe + s2 + var * R.Nq;
-      double acc = 0.0;
-      for (int a1 = 0; a1 <= p; ++a1) acc = fma(R.psi1[a1 * n + c1], y[(a1 * n + c2) * n + c3], acc);
-      t.base[e * t.pe + out + var * R.Nq + v] = acc;
-    }
-    __syncthreads();
-  }
-}
-
-// out = V^T in (nodal -> modal) with scratch s1, s2 (nodal-sized).
-template <int D>
-__device__ void apply_VT(const DevRef& R, const Tile& t, int in, int s1, int s2, int out, int nc) {
-  const int n = R.n, p = R.p;
-  if (D == 2) {
-    int rows = (p + 1) * n, tot = t.E * nc * rows;
-    for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
-      int row = idx % rows, ev = idx / rows, var = ev % nc, e = ev / nc;
-      int a1 = row / n, c2 = row % n;
-      const double* x = t.base + e * t.pe + in + var * R.Nq;
-      double acc = 0.0;
-      for (int c1 = 0; c1 < n; ++c1) acc = fma(R.psi1[a1 * n + c1], x[c1 + n * c2], acc);
-      t.base[e * t.pe + s1 + var * R.Nq + row] = acc;
-    }
-    __syncthreads();
-    rows = R.Np;
-    tot = t.E * nc * rows;
-    for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
-      int m = idx % rows, ev = idx / rows, var = ev % nc, e = ev / nc;
-      int a1 = R.mode[m];
-      const double* y = t.base + e * t.pe + s1 + var * R.Nq;
-      double acc = 0.0;
-      for (int c2 = 0; c2 < n; ++c2) acc = fma(R.psi2[m * n + c2], y[a1 * n + c2], acc);
-      t.base[e * t.pe + out + var * R.Np + m] = acc;
-    }
-    __syncthreads();
-  } else {
-    int rows = (p + 1) * n * n, tot = t.E * nc * rows;
-    for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
-      int row = idx % rows, ev = idx / rows, var = ev % nc, e = ev / nc;
-      int c3 = row % n, c2 = (row / n) % n, a1 = row / (n * n);
-      const double* x = t.base + e * t.pe + in + var * R.Nq;
-      double acc = 0.0;
-      for (int c1 = 0; c1 < n; ++c1) acc = fma(R.psi1[a1 * n + c1], x[c1 + n * (c2 + n * c3)], acc);
-      t.base[e * t.pe + s1 + var * R.Nq + row] = acc;
-    }
-    __syncthreads();
-    rows = R.S12 * n;
-    tot = t.E * nc * rows;
-    for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
-      int row = idx % rows, ev = idx / rows, var = ev % nc, e = ev / nc;
-      int s = row / n, c3 = row % n, a1 = R.s12a1[s];
-      const double* y = t.base + e * t.pe + s1 + var * R.Nq;
-      double acc = 0.0;
-      for (int c2 = 0; c2 < n; ++c2) acc = fma(R.psi2[s * n + c2], y[(a1 * n + c2) * n + c3], acc);
-      t.base[e * t.pe + s2 + var * R.Nq + row] = acc;
-    }
-    __syncthreads();
-    rows = R.Np;
-    tot = t.E * nc * rows;
-    for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
-      int m = idx % rows, ev = idx / rows, var = ev % nc, e = ev / nc;
-      int s = R.mode[m];
-      const double* y = t.base + e * t.pe + s2 + var * R.Nq;
-      double acc = 0.0;
-      for (int c3 = 0; c3 < n; ++c3) acc = fma(R.psi3[m * n + c3], y[s * n + c3], acc);
-      t.base[e * t.pe + out + var * R.Np + m] = acc;
-    }
-    __syncthreads();
-  }
-}
-
-// facet values wf = R^(zeta) w (Eq. (r_2d), Eq. (r_3d)); `y` is nodal scratch (tetrahedra).
-template <int D>
-__device__ void apply_R(const DevRef& R, const Tile& t, int in, int y, int out, int nc) {
-  const int n = R.n;
-  if (D == 3) {
-    int rows = n * n, tot = t.E * nc * rows;
-    for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {  // face 4: extrapolate eta3 -> -1
-      int row = idx % rows, ev = idx / rows, var = ev % nc, e = ev / nc;
-      const double* w = t.base + e * t.pe + in + var * R.Nq;
-      double acc = 0.0;
-      for (int c3 = 0; c3 < n; ++c3) acc = fma(R.l3m[c3], w[row + n * n * c3], acc);
-      t.base[e * t.pe + y + var * R.Nq + row] = acc;
-    }
-    __syncthreads();
-  }
-  int tot = t.E * nc * R.Nfn;
-  for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
-    int f = idx % R.Nfn, ev = idx / R.Nfn, var = ev % nc, e = ev / nc;
-    int z = f / R.Nqf, j = f % R.Nqf;
-    const double* w = t.base + e * t.pe + in + var * R.Nq;
-    double acc = 0.0;
-    if (D == 2) {
-      if (z == 0)
-        for (int b = 0; b < n; ++b) acc = fma(R.l2m[b], w[j + n * b], acc);
-      else {
-        const double* l = z == 1 ? R.l1p : R.l1m;
-        for (int a = 0; a < n; ++a) acc = fma(l[a], w[a + n * j], acc);
-      }
-    } else {
-      int a = j % n, b = j / n;
-      if (z == 0) {
-        for (int c2 = 0; c2 < n; ++c2) acc = fma(R.l2m[c2], w[a + n * (c2 + n * b)], acc);
-      } else if (z < 3) {
-        const double* l = z == 1 ? R.l1p : R.l1m;
-        for (int c1 = 0; c1 < n; ++c1) acc = fma(l[c1], w[c1 + n * j], acc);
-      } else {
-        const double* yy = t.base + e * t.pe + y + var * R.Nq;
-        for (int c2 = 0; c2 < n; ++c2) acc = fma(R.L2J[b * n + c2], yy[a + n * c2], acc);
-      }
-    }
-    t.base[e * t.pe + out + var * R.Nfn + f] = acc;
-  }
-  __syncthreads();
-}
-
-// ---------------------------------------------------------------------------
-// Pointwise maps
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ bool finite_pos(double x) { return x > 0.0 && x < 1.0e300; }
-
-// entropy variables W(u) = grad_U S (Section 7.1), times the weight W J
-template <int D>
-__device__ __forceinline__ void entropy_vars(const double* u, double gamma, double scale, double* w, int* bad) {
-  double rho = u[0];
-  double ir = 1.0 / rho, vv = 0.0, v[D];
-#pragma unroll
-  for (int k = 0; k < D; ++k) {
-    v[k] = u[1 + k] * ir;
-    vv = fma(v[k], v[k], vv);
-  }
-  double p = (gamma - 1.0) * (u[D + 1] - 0.5 * rho * vv);
-  if (!finite_pos(rho) || !finite_pos(p)) *bad = 1;
-  double s = log(p) - gamma * log(rho);
-  double b = rho / p;
-  w[0] = scale * ((gamma - s) / (gamma - 1.0) - 0.5 * b * vv);
-#pragma unroll
-  for (int k = 0; k < D; ++k) w[1 + k] = scale * b * v[k];
-  w[D + 1] = -scale * b;
-}
-
-// conservative variables U(w) (inverse of the entropy-variable map) returned as the
-// flux state: b = -w_last = rho/p, v = w_v/b, s = gamma - (gamma-1)(w_1 + b|v|^2/2),
-// ln rho = -(s + ln b)/(gamma-1), p = rho/b.
-template <int D>
-__device__ __forceinline__ NodeState<D> state_from_entropy(const double* w, double gamma, int* bad) {
-  NodeState<D> st;
-  double b = -w[D + 1];
-  if (!finite_pos(b)) *bad = 1;
-  double ib = 1.0 / b, vv = 0.0;
-#pragma unroll
-  for (int k = 0; k < D; ++k) {
-    st.v[k] = w[1 + k] * ib;
-    vv = fma(st.v[k], st.v[k], vv);
-  }
-  double s = gamma - (gamma - 1.0) * (w[0] + 0.5 * b * vv);
-  double lb = log(b);
-  st.lrho = -(s + lb) / (gamma - 1.0);
-  st.rho = exp(st.lrho);
-  st.p = st.rho * ib;
-  st.beta = b;
-  st.lbeta = lb;
-  if (!finite_pos(st.rho) || !finite_pos(st.p)) *bad = 1;
-  return st;
-}
-
-template <int D>
-__device__ __forceinline__ void store_state(double* S, int stride, int idx, const NodeState<D>& s) {
-  S[idx] = s.rho;
-#pragma unroll
-  for (int k = 0; k < D; ++k) S[(1 + k) * stride + idx] = s.v[k];
-  S[(D + 1) * stride + idx] = s.p;
-  S[(D + 2) * stride + idx] = s.beta;
-  S[(D + 3) * stride + idx] = s.lrho;
-  S[(D + 4) * stride + idx] = s.lbeta;
-}
-
-// ---------------------------------------------------------------------------
-// Projection kernel
-// shared layout per element (doubles): M[nc*Np] | A[nc*Nq] | B[nc*Nq] | C[nc*Nq] | F[nc*Nfn]
-// ---------------------------------------------------------------------------
-template <int D>
-__device__ void project_tile(const DevRef& R, const DevMesh& M, int64_t e0, int E, const double* __restrict__ u,
-                             double* __restrict__ w_modal) {
-  extern __shared__ double sm[];
-  constexpr int NC = D + 2, NF = D + 5;
-  const int Np = R.Np, Nq = R.Nq, Nfn = R.Nfn, Ntot = R.Ntot;
-  const int oM = 0, oA = NC * Np, oB = oA + NC * Nq, oC = oB + NC * Nq, oF = oC + NC * Nq;
-  const int pe = oF + NC * Nfn;
-  Tile t{sm, pe, E};
-  // 1. load u~
-  for (int idx = threadIdx.x; idx < E * NC * Np; idx += blockDim.x) {
-    int e = idx / (NC * Np), r = idx % (NC * Np);
-    sm[e * pe + oM + r] = u[(e0 + e) * NC * Np + r];
-  }
-  __syncthreads();
-  // 2. u = V u~
-  apply_V<D>(R, t, oM, oB, oC, oA, NC);
-  // 3. W J W(u)
-  int lbad = 0;
-  for (int idx = threadIdx.x; idx < E * Nq; idx += blockDim.x) {
-    int e = idx / Nq, v = idx % Nq;
-    double uu[NC], ww[NC];
-    double* A = sm + e * pe + oA;
-#pragma unroll
-    for (int c = 0; c < NC; ++c) uu[c] = A[c * Nq + v];
-    entropy_vars<D>(uu, M.gamma, M.wj[(e0 + e) * Nq + v], ww, &lbad);
-#pragma unroll
-    for (int c = 0; c < NC; ++c) A[c * Nq + v] = ww[c];
-  }
-  __syncthreads();
-  // 4-6. w~ = V^T (W/J) V V^T (W J W)
-  apply_VT<D>(R, t, oA, oB, oC, oM, NC);
-  apply_V<D>(R, t, oM, oB, oC, oA, NC);
-  for (int idx = threadIdx.x; idx < E * NC * Nq; idx += blockDim.x) {
-    int e = idx / (NC * Nq), v = idx % Nq;
-    sm[e * pe + oA + idx % (NC * Nq)] *= M.wdj[(e0 + e) * Nq + v];
-  }
-  __syncthreads();
-  apply_VT<D>(R, t, oA, oB, oC, oM, NC);
-  if (w_modal) {
-    for (int idx = threadIdx.x; idx < E * NC * Np; idx += blockDim.x) {
-      int e = idx / (NC * Np), r = idx % (NC * Np);
-      w_modal[(e0 + e) * NC * Np + r] = sm[e * pe + oM + r];
-    }
-    if (lbad) atomicOr(M.flag, 1);
-    return;
-  }
-  // 7-8. w = V w~, facet values R w
-  apply_V<D>(R, t, oM, oB, oC, oA, NC);
-  apply_R<D>(R, t, oA, oB, oF, NC);
-  // 9. entropy-projected conservative states at volume and facet nodes
-  for (int idx = threadIdx.x; idx < E * Ntot; idx += blockDim.x) {
-    int e = idx / Ntot, k = idx % Ntot;
-    double ww[NC];
-    const double* src = k < Nq ? sm + e * pe + oA + k : sm + e * pe + oF + (k - Nq);
-    const int str = k < Nq ? Nq : Nfn;
-#pragma unroll
-    for (int c = 0; c < NC; ++c) ww[c] = src[c * str];
-    NodeState<D> st = state_from_entropy<D>(ww, M.gamma, &lbad);
-    store_state<D>(M.states + (e0 + e) * NF * Ntot, Ntot, k, st);
-    if (k >= Nq) M.cfac[(e0 + e) * Nfn + (k - Nq)] = sqrt(M.gamma * st.p / st.rho);
-  }
-  if (lbad) atomicOr(M.flag, 1);
-}
 
 template <int D>
 __global__ void project_kernel(DevRef R, DevMesh M, int epc, const double* __restrict__ u,
@@ -405,316 +28,6 @@ __global__ void project_kernel(DevRef R, DevMesh M, int epc, const double* __res
   const int64_t e0 = (int64_t)blockIdx.x * epc;
   const int E = (int)((M.E - e0) < (int64_t)epc ? (M.E - e0) : (int64_t)epc);
   project_tile<D>(R, M, e0, E, u, w_modal);
-}
-
-// ---------------------------------------------------------------------------
-// Residual kernel
-// shared layout per element (doubles):
-//   region0 : states Sv[NF*Nq] | Sf[NF*Nfn] | part[NC*n^3] (tets)  -- reused as scratch later
-//   r[NC*Nq] | h[NC*Nfn]
-// ---------------------------------------------------------------------------
-struct ResLayout {
-  int oSv, oSf, oPart, oS1, oS2, oMod, oR, oH, pe;
-};
-
-template <int D>
-__host__ __device__ inline ResLayout res_layout(int Nq, int Nfn, int Np, int n) {
-  constexpr int NC = D + 2, NF = D + 5;
-  ResLayout L;
-  L.oSv = 0;
-  L.oSf = NF * Nq;
-  L.oPart = L.oSf + NF * Nfn;
-  int r0 = L.oPart + (D == 3 ? NC * n * n * n : 0);
-  L.oS1 = 0;
-  L.oS2 = NC * Nq;
-  L.oMod = 2 * NC * Nq;
-  int r0b = L.oMod + NC * Np;
-  if (r0b > r0) r0 = r0b;
-  L.oR = r0;
-  L.oH = L.oR + NC * Nq;
-  L.pe = L.oH + NC * Nfn;
-  return L;
-}
-
-template <int D>
-__device__ __forceinline__ void load_dir(const double* base, int slot, int T, int t, double* n) {
-#pragma unroll
-  for (int k = 0; k < D; ++k) n[k] = base[(slot * D + k) * T + t];
-}
-
-template <int D>
-__device__ void residual_tile(const DevRef& R, const DevMesh& M, int64_t e0, int E, const Epilogue& ep) {
-  extern __shared__ double sm[];
-  constexpr int NC = D + 2, NF = D + 5;
-  const int n = R.n, Nq = R.Nq, Nfn = R.Nfn, Ntot = R.Ntot, Np = R.Np, T = R.T, Nqf = R.Nqf;
-  const ResLayout Ly = res_layout<D>(Nq, Nfn, Np, n);
-  const int pe = Ly.pe;
-  const double inv_gm1 = 1.0 / (M.gamma - 1.0);
-  Tile tile{sm, pe, E};
-
-  // 1. load states
-  for (int idx = threadIdx.x; idx < E * NF * Ntot; idx += blockDim.x) {
-    int e = idx / (NF * Ntot), r = idx % (NF * Ntot), f = r / Ntot, k = r % Ntot;
-    double val = M.states[(e0 + e) * NF * Ntot + r];
-    if (k < Nq)
-      sm[e * pe + Ly.oSv + f * Nq + k] = val;
-    else
-      sm[e * pe + Ly.oSf + f * Nfn + (k - Nq)] = val;
-  }
-  for (int idx = threadIdx.x; idx < E * NC * Nq; idx += blockDim.x) {
-    int e = idx / (NC * Nq);
-    sm[e * pe + Ly.oR + idx % (NC * Nq)] = 0.0;
-  }
-  __syncthreads();
-  // 2. interface flux h = B J f* (Eq. (interface_flux), Eq. (num_flux), Eq. (wave_speed))
-  for (int idx = threadIdx.x; idx < E * Nfn; idx += blockDim.x) {
-    int e = idx / Nfn, f = idx % Nfn;
-    const int64_t eg = e0 + e;
-    NodeState<D> L = load_state<D>(sm + e * pe + Ly.oSf, Nfn, f);
-    const int64_t e2 = M.nbr_e[eg * Nfn + f];
-    const int f2 = M.nbr_f[eg * Nfn + f];
-    NodeState<D> Rr = load_state<D>(M.states + e2 * NF * Ntot + Nq, Ntot, f2);
-    double nn[D];
-#pragma unroll
-    for (int k = 0; k < D; ++k) nn[k] = M.nrm[(eg * D + k) * Nfn + f];
-    double F[NC];
-    ec_flux<D>(L, Rr, nn, inv_gm1, F);
-    if (M.lf) {
-      double vnL = 0.0, vnR = 0.0, vvL = 0.0, vvR = 0.0;
-#pragma unroll
-      for (int k = 0; k < D; ++k) {
-        vnL = fma(L.v[k], nn[k], vnL);
-        vnR = fma(Rr.v[k], nn[k], vnR);
-        vvL = fma(L.v[k], L.v[k], vvL);
-        vvR = fma(Rr.v[k], Rr.v[k], vvR);
-      }
-      double lam = fmax(fabs(vnL), fabs(vnR)) + fmax(M.cfac[eg * Nfn + f], M.cfac[e2 * Nfn + f2]);
-      double hl = 0.5 * lam;
-      F[0] -= hl * (Rr.rho - L.rho);
-#pragma unroll
-      for (int k = 0; k < D; ++k) F[1 + k] -= hl * (Rr.rho * Rr.v[k] - L.rho * L.v[k]);
-      double EL = L.p * inv_gm1 + 0.5 * L.rho * vvL, ER = Rr.p * inv_gm1 + 0.5 * Rr.rho * vvR;
-      F[D + 1] -= hl * (ER - EL);
-    }
-    const double bj = M.bj[eg * Nfn + f];
-    double* h = sm + e * pe + Ly.oH;
-#pragma unroll
-    for (int c = 0; c < NC; ++c) h[c * Nfn + f] = bj * F[c];
-  }
-  __syncthreads();
-  // 3. line-based flux differencing and facet correction
-  const int tid = threadIdx.x;
-  const int el = tid / T, t = tid % T;
-  const bool active = el < E;
-  const int64_t eg = e0 + el;
-  const double* vdir = active ? M.vdir + eg * (int64_t)R.nvp * D : nullptr;
-  const double* fdir = active ? M.fdir + eg * (int64_t)R.nfp * D : nullptr;
-  double* Sv = sm + el * pe + Ly.oSv;
-  double* Sf = sm + el * pe + Ly.oSf;
-  double* r = sm + el * pe + Ly.oR;
-  double* h = sm + el * pe + Ly.oH;
-  for (int ph = 0; ph < D; ++ph) {
-    if (active) {
-      // node index along the line of this task
-      int base, stride;
-      if (D == 2) {
-        base = ph == 0 ? n * t : t;
-        stride = ph == 0 ? 1 : n;
-      } else {
-        if (ph == 0) { base = n * t; stride = 1; }
-        else if (ph == 1) { base = (t % n) + n * n * (t / n); stride = n; }
-        else { base = t; stride = n * n; }
-      }
-      int m = 0;
-      for (int a = 0; a < n; ++a) {
-        const int vi = base + a * stride;
-        NodeState<D> Si = load_state<D>(Sv, Nq, vi);
-        for (int b = a + 1; b < n; ++b, ++m) {
-          const int vj = base + b * stride;
-          NodeState<D> Sj = load_state<D>(Sv, Nq, vj);
-          double nn[D], F[NC];
-          load_dir<D>(vdir, ph * R.Lv + m, T, t, nn);
-          ec_flux<D>(Si, Sj, nn, inv_gm1, F);
-#pragma unroll
-          for (int c = 0; c < NC; ++c) {
-            r[c * Nq + vi] -= F[c];
-            r[c * Nq + vj] += F[c];
-          }
-        }
-      }
-      // facet correction pairs lying on these lines
-      if (ph == 0) {
-        const double* fd = fdir + R.fph_off[0];
-        for (int zz = 0; zz < 2; ++zz) {
-          const int f = (1 + zz) * Nqf + t;
-          NodeState<D> Sfj = load_state<D>(Sf, Nfn, f);
-          for (int a = 0; a < n; ++a) {
-            const int vi = base + a * stride;
-            NodeState<D> Si = load_state<D>(Sv, Nq, vi);
-            double nn[D], F[NC];
-            load_dir<D>(fd, zz * n + a, T, t, nn);
-            ec_flux<D>(Si, Sfj, nn, inv_gm1, F);
-#pragma unroll
-            for (int c = 0; c < NC; ++c) {
-              r[c * Nq + vi] -= F[c];
-              h[c * Nfn + f] -= F[c];
-            }
-          }
-        }
-      } else if (ph == 1) {
-        const double* fd = fdir + R.fph_off[1];
-        const int f = t;
-        NodeState<D> Sfj = load_state<D>(Sf, Nfn, f);
-        for (int b = 0; b < n; ++b) {
-          const int vi = base + b * stride;
-          NodeState<D> Si = load_state<D>(Sv, Nq, vi);
-          double nn[D], F[NC];
-          load_dir<D>(fd, b, T, t, nn);
-          ec_flux<D>(Si, Sfj, nn, inv_gm1, F);
-#pragma unroll
-          for (int c = 0; c < NC; ++c) {
-            r[c * Nq + vi] -= F[c];
-            h[c * Nfn + f] -= F[c];
-          }
-        }
-      }
-    }
-    __syncthreads();
-  }
-  if (D == 3) {
-    // face 4: task t = a + n*b2 owns volume nodes (a, b2, b3); facet nodes (a, b') get
-    // per-task partial sums that are reduced below.
-    double* part = sm + el * pe + Ly.oPart;
-    if (active) {
-      const int a = t % n, b2 = t / n;
-      const double* fd = fdir + R.fph_off[3];
-      int m = 0;
-      for (int bp = 0; bp < n; ++bp) {
-        const int f = 3 * Nqf + a + n * bp;
-        NodeState<D> Sfj = load_state<D>(Sf, Nfn, f);
-        double acc[NC];
-#pragma unroll
-        for (int c = 0; c < NC; ++c) acc[c] = 0.0;
-        for (int b3 = 0; b3 < n; ++b3, ++m) {
-          const int vi = a + n * (b2 + n * b3);
-          NodeState<D> Si = load_state<D>(Sv, Nq, vi);
-          double nn[D], F[NC];
-          load_dir<D>(fd, m, T, t, nn);
-          ec_flux<D>(Si, Sfj, nn, inv_gm1, F);
-#pragma unroll
-          for (int c = 0; c < NC; ++c) {
-            r[c * Nq + vi] -= F[c];
-            acc[c] += F[c];
-          }
-        }
-#pragma unroll
-        for (int c = 0; c < NC; ++c) part[(c * T + t) * n + bp] = acc[c];
-      }
-    }
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < E * NC * Nqf; idx += blockDim.x) {
-      int e = idx / (NC * Nqf), rr = idx % (NC * Nqf), c = rr / Nqf, j = rr % Nqf;
-      int a = j % n, bp = j / n;
-      const double* pp = sm + e * pe + Ly.oPart + c * T * n;
-      double s = 0.0;
-      for (int b2 = 0; b2 < n; ++b2) s += pp[(a + n * b2) * n + bp];
-      sm[e * pe + Ly.oH + c * Nfn + 3 * Nqf + j] -= s;
-    }
-    __syncthreads();
-  }
-  // 4. lift: r -= sum_zeta R^T h  (h = B J f* - C^T 1)
-  if (D == 3) {
-    // y[a + n*b2] = sum_b' L2J[b'][b2] h4[a + n*b']  (into scratch part region, free now)
-    for (int idx = threadIdx.x; idx < E * NC * n * n; idx += blockDim.x) {
-      int e = idx / (NC * n * n), rr = idx % (NC * n * n), c = rr / (n * n), ab = rr % (n * n);
-      int a = ab % n, b2 = ab / n;
-      const double* hh = sm + e * pe + Ly.oH + c * Nfn + 3 * Nqf;
-      double s = 0.0;
-      for (int bp = 0; bp < n; ++bp) s = fma(R.L2J[bp * n + b2], hh[a + n * bp], s);
-      sm[e * pe + Ly.oPart + rr] = s;
-    }
-    __syncthreads();
-  }
-  for (int idx = threadIdx.x; idx < E * NC * Nq; idx += blockDim.x) {
-    int e = idx / (NC * Nq), rr = idx % (NC * Nq), c = rr / Nq, v = rr % Nq;
-    const double* hh = sm + e * pe + Ly.oH + c * Nfn;
-    double s;
-    if (D == 2) {
-      int a = v % n, b = v / n;
-      s = R.l2m[b] * hh[a] + R.l1p[a] * hh[Nqf + b] + R.l1m[a] * hh[2 * Nqf + b];
-    } else {
-      int a = v % n, b = (v / n) % n, c3 = v / (n * n);
-      const double* y = sm + e * pe + Ly.oPart + c * n * n;
-      s = R.l2m[b] * hh[a + n * c3] + R.l1p[a] * hh[Nqf + b + n * c3] + R.l1m[a] * hh[2 * Nqf + b + n * c3] +
-          R.l3m[c3] * y[a + n * b];
-    }
-    sm[e * pe + Ly.oR + rr] -= s;
-  }
-  __syncthreads();
-  if (ep.mode == 2) {
-    // diagnostics: per element sum_i r_i (per variable), sum w.r, sum |w r|
-    for (int e = threadIdx.x / 32; e < E; e += blockDim.x / 32) {
-      const int lane = threadIdx.x % 32;
-      double acc[NC + 2];
-#pragma unroll
-      for (int c = 0; c < NC + 2; ++c) acc[c] = 0.0;
-      for (int v = lane; v < Nq; v += 32) {
-        NodeState<D> s = load_state<D>(sm + e * pe + Ly.oSv, Nq, v);
-        double vv = 0.0;
-#pragma unroll
-        for (int k = 0; k < D; ++k) vv += s.v[k] * s.v[k];
-        double sent = (1.0 - M.gamma) * s.lrho - s.lbeta;   // ln(p / rho^gamma)
-        double w[NC];
-        w[0] = (M.gamma - sent) * inv_gm1 - 0.5 * s.beta * vv;
-#pragma unroll
-        for (int k = 0; k < D; ++k) w[1 + k] = s.beta * s.v[k];
-        w[D + 1] = -s.beta;
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-          double rv = sm[e * pe + Ly.oR + c * Nq + v];
-          acc[c] += rv;
-          acc[NC] += w[c] * rv;
-          acc[NC + 1] += fabs(w[c] * rv);
-        }
-      }
-#pragma unroll
-      for (int c = 0; c < NC + 2; ++c) {
-        double x = acc[c];
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-        if (lane == 0) ep.diag[(e0 + e) * (NC + 2) + c] = x;
-      }
-    }
-    return;
-  }
-  // 5. d u~/dt = V^T (W/J) V (V^T r)   (Eq. (matvec_dudt), M = I)
-  apply_VT<D>(R, tile, Ly.oR, Ly.oS1, Ly.oS2, Ly.oMod, NC);
-  apply_V<D>(R, tile, Ly.oMod, Ly.oS1, Ly.oS2, Ly.oR, NC);
-  for (int idx = threadIdx.x; idx < E * NC * Nq; idx += blockDim.x) {
-    int e = idx / (NC * Nq), v = idx % Nq;
-    sm[e * pe + Ly.oR + idx % (NC * Nq)] *= M.wdj[(e0 + e) * Nq + v];
-  }
-  __syncthreads();
-  apply_VT<D>(R, tile, Ly.oR, Ly.oS1, Ly.oS2, Ly.oMod, NC);
-  // 6. epilogue
-  for (int idx = threadIdx.x; idx < E * NC * Np; idx += blockDim.x) {
-    int e = idx / (NC * Np), rr = idx % (NC * Np);
-    const int64_t g = (e0 + e) * NC * Np + rr;
-    double k = sm[e * pe + Ly.oMod + rr];
-    if (ep.mode == 0) {
-      ep.dudt[g] = k;
-    } else {
-      double acc = ep.acc_in[g] + ep.cb * k;
-      if (ep.stage_out) ep.stage_out[g] = ep.u0[g] + ep.ca * k;
-      ep.acc_out[g] = acc;
-    }
-  }
-}
-
-template <int D>
-__global__ void residual_kernel(DevRef R, DevMesh M, int epc, Epilogue ep) {
-  const int64_t e0 = (int64_t)blockIdx.x * epc;
-  const int E = (int)((M.E - e0) < (int64_t)epc ? (M.E - e0) : (int64_t)epc);
-  residual_tile<D>(R, M, e0, E, ep);
 }
 
 // ---------------------------------------------------------------------------
@@ -733,16 +46,6 @@ __global__ void project_batch_kernel(const BatchMesh* __restrict__ meshes, const
   }
 }
 
-template <int D>
-__global__ void residual_batch_kernel(const BatchMesh* __restrict__ meshes, const BatchItem* __restrict__ items,
-                                      int nitems) {
-  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-    const BatchItem w = items[it];
-    const BatchMesh& bm = meshes[w.mesh];
-    residual_tile<D>(bm.R, bm.M, w.e0, w.E, bm.ep);
-    __syncthreads();
-  }
-}
 
 // ---------------------------------------------------------------------------
 // Reference L2 projection u~ = V^T W u of nodal input data (input preparation)
@@ -769,264 +72,6 @@ __global__ void l2_project_kernel(DevRef R, DevMesh M, int epc, const double* __
   }
 }
 
-// ---------------------------------------------------------------------------
-// Vector-Jacobian product (reverse mode, hand-derived; not in the paper)
-//
-// Per-node cotangents are carried for the primitive triple q = (rho, v, p); the
-// derived fields beta = rho/p, ln rho, ln beta are functions of q and their
-// cotangents are folded back inside the pair adjoint.
-// ---------------------------------------------------------------------------
-
-// log mean and its partial derivatives, with the same branches as log_mean():
-// series branch, LM = (a+b)/(2F(u)), F = 1 + u/3 + u^2/5 + u^3/7, u = ((b-a)/(a+b))^2:
-//   dLM/da = 1/(2F) + 2 f b F'(u)/((a+b) F^2),  dLM/db = 1/(2F) - 2 f a F'(u)/((a+b) F^2)
-// direct branch, LM = (b-a)/L, L = ln b - ln a:
-//   dLM/da = (LM/a - 1)/L,  dLM/db = (1 - LM/b)/L
-__device__ __forceinline__ void log_mean_grad(double a, double b, double la, double lb, double* lm, double* da,
-                                              double* db) {
-  double s = a + b, d = b - a, f = d / s, u = f * f;
-  if (u < 1.0e-4) {
-    double F = 1.0 + u * (1.0 / 3.0 + u * (1.0 / 5.0 + u * (1.0 / 7.0)));
-    double Fp = 1.0 / 3.0 + u * (2.0 / 5.0 + u * (3.0 / 7.0));
-    *lm = s / (2.0 + u * (2.0 / 3.0 + u * (2.0 / 5.0 + u * (2.0 / 7.0))));
-    double t = 2.0 * f * Fp / (s * F * F);
-    *da = 0.5 / F + t * b;
-    *db = 0.5 / F - t * a;
-  } else {
-    double L = lb - la, m = d / L;
-    *lm = m;
-    *da = (m / a - 1.0) / L;
-    *db = (1.0 - m / b) / L;
-  }
-}
-
-// Adds (d F/d qL)^T Fb to qL and (d F/d qR)^T Fb to qR for the directional flux of ec_flux.
-template <int D>
-__device__ __forceinline__ void ec_flux_adj(const NodeState<D>& L, const NodeState<D>& R, const double* n,
-                                            double inv_gm1, const double* Fb, double* qL, double* qR) {
-  double rl, dra, drb, bl, dba, dbb;
-  log_mean_grad(L.rho, R.rho, L.lrho, R.lrho, &rl, &dra, &drb);
-  log_mean_grad(L.beta, R.beta, L.lbeta, R.lbeta, &bl, &dba, &dbb);
-  const double ib = 1.0 / bl;
-  double vnL = 0.0, vnR = 0.0, vv = 0.0;
-#pragma unroll
-  for (int k = 0; k < D; ++k) {
-    vnL = fma(n[k], L.v[k], vnL);
-    vnR = fma(n[k], R.v[k], vnR);
-    vv = fma(L.v[k], R.v[k], vv);
-  }
-  const double frho = rl * 0.5 * (vnL + vnR);
-  const double FE = Fb[D + 1];
-  double frho_b = Fb[0] + FE * (0.5 * vv + inv_gm1 * ib);
-  double pavg_b = 0.0;
-#pragma unroll
-  for (int k = 0; k < D; ++k) {
-    frho_b = fma(Fb[1 + k], 0.5 * (L.v[k] + R.v[k]), frho_b);
-    pavg_b = fma(Fb[1 + k], n[k], pavg_b);
-  }
-  const double vv_b = 0.5 * FE * frho;
-  const double ib_b = FE * frho * inv_gm1;
-  double pL_b = 0.5 * pavg_b + 0.5 * FE * vnR;
-  double pR_b = 0.5 * pavg_b + 0.5 * FE * vnL;
-  const double rl_b = frho_b * 0.5 * (vnL + vnR);
-  const double vnL_b = 0.5 * FE * R.p + 0.5 * frho_b * rl;
-  const double vnR_b = 0.5 * FE * L.p + 0.5 * frho_b * rl;
-#pragma unroll
-  for (int k = 0; k < D; ++k) {
-    const double vs_b = 0.5 * Fb[1 + k] * frho;
-    qL[1 + k] += vs_b + vv_b * R.v[k] + vnL_b * n[k];
-    qR[1 + k] += vs_b + vv_b * L.v[k] + vnR_b * n[k];
-  }
-  double rhoL_b = rl_b * dra, rhoR_b = rl_b * drb;
-  const double bl_b = -ib * ib * ib_b;
-  const double bL_b = bl_b * dba, bR_b = bl_b * dbb;
-  rhoL_b += bL_b / L.p;
-  pL_b -= bL_b * L.beta / L.p;
-  rhoR_b += bR_b / R.p;
-  pR_b -= bR_b * R.beta / R.p;
-  qL[0] += rhoL_b;
-  qR[0] += rhoR_b;
-  qL[D + 1] += pL_b;
-  qR[D + 1] += pR_b;
-}
-
-// adjoint of the interface flux f* = f#(q-, q+, n) - lambda/2 (U+ - U-) (Eq. (num_flux),
-// Eq. (wave_speed)); max/|.| use the sub-gradient with ties to the interior side.
-template <int D>
-__device__ __forceinline__ void iface_adj(const NodeState<D>& L, const NodeState<D>& R, const double* n,
-                                          double inv_gm1, double cL, double cR, int lf, const double* fb,
-                                          double* qL, double* qR) {
-  ec_flux_adj<D>(L, R, n, inv_gm1, fb, qL, qR);
-  if (!lf) return;
-  constexpr int NC = D + 2;
-  double vnL = 0.0, vnR = 0.0, vvL = 0.0, vvR = 0.0;
-#pragma unroll
-  for (int k = 0; k < D; ++k) {
-    vnL = fma(L.v[k], n[k], vnL);
-    vnR = fma(R.v[k], n[k], vnR);
-    vvL = fma(L.v[k], L.v[k], vvL);
-    vvR = fma(R.v[k], R.v[k], vvR);
-  }
-  const double lam = fmax(fabs(vnL), fabs(vnR)) + fmax(cL, cR);
-  double UL[NC], UR[NC];
-  UL[0] = L.rho;
-  UR[0] = R.rho;
-#pragma unroll
-  for (int k = 0; k < D; ++k) {
-    UL[1 + k] = L.rho * L.v[k];
-    UR[1 + k] = R.rho * R.v[k];
-  }
-  UL[D + 1] = L.p * inv_gm1 + 0.5 * L.rho * vvL;
-  UR[D + 1] = R.p * inv_gm1 + 0.5 * R.rho * vvR;
-  double lam_b = 0.0;
-#pragma unroll
-  for (int c = 0; c < NC; ++c) lam_b -= 0.5 * fb[c] * (UR[c] - UL[c]);
-  // U(q) adjoints with U+_b = -lam/2 fb, U-_b = +lam/2 fb
-  const double hl = 0.5 * lam;
-  {
-    double ER = -hl * fb[D + 1], EL = hl * fb[D + 1];
-    qR[0] += -hl * fb[0] + 0.5 * vvR * ER;
-    qL[0] += hl * fb[0] + 0.5 * vvL * EL;
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
-      qR[0] += -hl * fb[1 + k] * R.v[k];
-      qL[0] += hl * fb[1 + k] * L.v[k];
-      qR[1 + k] += -hl * fb[1 + k] * R.rho + ER * R.rho * R.v[k];
-      qL[1 + k] += hl * fb[1 + k] * L.rho + EL * L.rho * L.v[k];
-    }
-    qR[D + 1] += ER * inv_gm1;
-    qL[D + 1] += EL * inv_gm1;
-  }
-  if (fabs(vnL) >= fabs(vnR)) {
-    const double g = lam_b * (vnL > 0.0 ? 1.0 : (vnL < 0.0 ? -1.0 : 0.0));
-#pragma unroll
-    for (int k = 0; k < D; ++k) qL[1 + k] += g * n[k];
-  } else {
-    const double g = lam_b * (vnR > 0.0 ? 1.0 : (vnR < 0.0 ? -1.0 : 0.0));
-#pragma unroll
-    for (int k = 0; k < D; ++k) qR[1 + k] += g * n[k];
-  }
-  if (cL >= cR) {
-    qL[D + 1] += lam_b * cL / (2.0 * L.p);
-    qL[0] -= lam_b * cL / (2.0 * L.rho);
-  } else {
-    qR[D + 1] += lam_b * cR / (2.0 * R.p);
-    qR[0] -= lam_b * cR / (2.0 * R.rho);
-  }
-}
-
-// (dq/dw)^T qb for q = (rho, v, p) = U(w) written through the entropy variables:
-// b = -w_last, v = w_v/b, ln rho = -(s + ln b)/(gamma-1), s = gamma - (gamma-1)(w_1 + b|v|^2/2), p = rho/b.
-template <int D>
-__device__ __forceinline__ void qbar_to_wbar(const NodeState<D>& s, const double* qb, double gamma, double* wb) {
-  double vv = 0.0;
-#pragma unroll
-  for (int k = 0; k < D; ++k) vv = fma(s.v[k], s.v[k], vv);
-  const double b = s.beta;
-  const double Lb = qb[0] * s.rho + qb[D + 1] * s.p;   // cotangent of ln rho
-  double bb = -qb[D + 1] * s.p / b + Lb * (-0.5 * vv - 1.0 / ((gamma - 1.0) * b));
-#pragma unroll
-  for (int k = 0; k < D; ++k) {
-    bb -= qb[1 + k] * s.v[k] / b;
-    wb[1 + k] = Lb * s.v[k] + qb[1 + k] / b;
-  }
-  wb[0] = Lb;
-  wb[D + 1] = -bb;
-}
-
-// (d W/du)^T g for the entropy variables of the conservative state u (Section 7.1).
-template <int D>
-__device__ __forceinline__ void entropy_vars_adj(const double* u, double gamma, const double* g, double* ub) {
-  const double rho = u[0];
-  double v[D], vv = 0.0;
-#pragma unroll
-  for (int k = 0; k < D; ++k) {
-    v[k] = u[1 + k] / rho;
-    vv = fma(v[k], v[k], vv);
-  }
-  const double p = (gamma - 1.0) * (u[D + 1] - 0.5 * rho * vv);
-  const double b = rho / p;
-  double bb = -g[D + 1] - 0.5 * vv * g[0];
-  double vb[D];
-#pragma unroll
-  for (int k = 0; k < D; ++k) {
-    bb += g[1 + k] * v[k];
-    vb[k] = g[1 + k] * b - g[0] * b * v[k];
-  }
-  const double sb = -g[0] / (gamma - 1.0);
-  const double pb = sb / p - bb * b / p;
-  const double rb = -sb * gamma / rho + bb / p;
-  ub[D + 1] = pb * (gamma - 1.0);
-  double r = rb + pb * (gamma - 1.0) * 0.5 * vv;
-#pragma unroll
-  for (int k = 0; k < D; ++k) {
-    ub[1 + k] = vb[k] / rho - pb * (gamma - 1.0) * v[k];
-    r -= vb[k] * v[k] / rho;
-  }
-  ub[0] = r;
-}
-
-// out (nodal, += sign * R^T in) with scratch y (tetrahedra)
-template <int D>
-__device__ void apply_RT(const DevRef& R, const Tile& t, int in, int y, int out, int nc, double sign) {
-  const int n = R.n, Nq = R.Nq, Nfn = R.Nfn, Nqf = R.Nqf;
-  if (D == 3) {
-    for (int idx = threadIdx.x; idx < t.E * nc * n * n; idx += blockDim.x) {
-      int e = idx / (nc * n * n), rr = idx % (nc * n * n), c = rr / (n * n), ab = rr % (n * n);
-      int a = ab % n, b2 = ab / n;
-      const double* hh = t.base + e * t.pe + in + c * Nfn + 3 * Nqf;
-      double s = 0.0;
-      for (int bp = 0; bp < n; ++bp) s = fma(R.L2J[bp * n + b2], hh[a + n * bp], s);
-      t.base[e * t.pe + y + rr] = s;
-    }
-    __syncthreads();
-  }
-  for (int idx = threadIdx.x; idx < t.E * nc * Nq; idx += blockDim.x) {
-    int e = idx / (nc * Nq), rr = idx % (nc * Nq), c = rr / Nq, v = rr % Nq;
-    const double* hh = t.base + e * t.pe + in + c * Nfn;
-    double s;
-    if (D == 2) {
-      int a = v % n, b = v / n;
-      s = R.l2m[b] * hh[a] + R.l1p[a] * hh[Nqf + b] + R.l1m[a] * hh[2 * Nqf + b];
-    } else {
-      int a = v % n, b = (v / n) % n, c3 = v / (n * n);
-      const double* yy = t.base + e * t.pe + y + c * n * n;
-      s = R.l2m[b] * hh[a + n * c3] + R.l1p[a] * hh[Nqf + b + n * c3] + R.l1m[a] * hh[2 * Nqf + b + n * c3] +
-          R.l3m[c3] * yy[a + n * b];
-    }
-    t.base[e * t.pe + out + rr] += sign * s;
-  }
-  __syncthreads();
-}
-
-// Residual adjoint: cot (cotangent of d u~/dt) -> per-node cotangents of q at own volume
-// and facet nodes (qbar [E][NQ][Ntot]) and, per facet node, the cotangent of the
-// neighbour's state through this element's interface flux (qext [E][NQ][Nfn]).
-struct AdjLayout {
-  int oReg, oM, oS1, oS2, oSv, oSf, oRb, oHb, oQv, oQf, oPart, pe;
-};
-
-template <int D>
-__host__ __device__ inline AdjLayout adj_layout(int Nq, int Nfn, int Np, int n) {
-  constexpr int NC = D + 2, NF = D + 5, NQ = D + 2;
-  AdjLayout L;
-  L.oReg = 0;
-  L.oS1 = 0;
-  L.oS2 = NC * Nq;
-  L.oM = 2 * NC * Nq;
-  L.oSv = 0;
-  L.oSf = NF * Nq;
-  int r0 = 2 * NC * Nq + NC * Np;
-  if (NF * (Nq + Nfn) > r0) r0 = NF * (Nq + Nfn);
-  L.oRb = r0;
-  L.oHb = L.oRb + NC * Nq;
-  L.oQv = L.oHb + NC * Nfn;
-  L.oQf = L.oQv + NQ * Nq;
-  L.oPart = L.oQf + NQ * Nfn;
-  L.pe = L.oPart + (D == 3 ? NQ * n * n * n : 0);
-  return L;
-}
-
 template <int D>
 __global__ void residual_adjoint_kernel(DevRef R, DevMesh M, int epc, const double* __restrict__ cot,
                                         double* __restrict__ qbar, double* __restrict__ qext) {
@@ -1045,13 +90,12 @@ __global__ void residual_adjoint_kernel(DevRef R, DevMesh M, int epc, const doub
     sm[e * pe + Ly.oM + r] = cot[(e0 + e) * NC * Np + r];
   }
   __syncthreads();
-  apply_V<D>(R, tile, Ly.oM, Ly.oS1, Ly.oS2, Ly.oRb, NC);
-  for (int idx = threadIdx.x; idx < E * NC * Nq; idx += blockDim.x) {
-    int e = idx / (NC * Nq), v = idx % Nq;
-    sm[e * pe + Ly.oRb + idx % (NC * Nq)] *= M.wdj[(e0 + e) * Nq + v];
+  apply_minv<D>(R, M, tile, e0, Ly.oM, Ly.oS1, Ly.oS2, Ly.oRb, Ly.oRb, NC);
+  for (int idx = threadIdx.x; idx < E * NC * Np; idx += blockDim.x) {
+    int e = idx / (NC * Np);
+    sm[e * pe + Ly.oM + idx % (NC * Np)] = sm[e * pe + Ly.oRb + idx % (NC * Np)];
   }
   __syncthreads();
-  apply_VT<D>(R, tile, Ly.oRb, Ly.oS1, Ly.oS2, Ly.oM, NC);
   apply_V<D>(R, tile, Ly.oM, Ly.oS1, Ly.oS2, Ly.oRb, NC);
   // 2. h_b = -R r_b  (r -= R^T h in the forward)
   apply_R<D>(R, tile, Ly.oRb, Ly.oS1, Ly.oHb, NC);
@@ -1269,14 +313,13 @@ __global__ void project_adjoint_kernel(DevRef R, DevMesh M, int epc, const doubl
   // 2. w_b += R^T w_b^f ; 3. w~_b = V^T w_b
   apply_RT<D>(R, t, oF, oB, oA, NC, 1.0);
   apply_VT<D>(R, t, oA, oB, oC, oM, NC);
-  // 4. g = V V^T (W/J) V w~_b   (transpose of w~ = V^T (W/J) V V^T g)
-  apply_V<D>(R, t, oM, oB, oC, oA, NC);
-  for (int idx = threadIdx.x; idx < E * NC * Nq; idx += blockDim.x) {
-    int e = idx / (NC * Nq), v = idx % Nq;
-    sm[e * pe + oA + idx % (NC * Nq)] *= M.wdj[(e0 + e) * Nq + v];
+  // 4. g = V [V^T (W/J) V] w~_b   (transpose of w~ = V^T (W/J) V V^T g)
+  apply_minv<D>(R, M, t, e0, oM, oB, oC, oA, oA, NC);
+  for (int idx = threadIdx.x; idx < E * NC * Np; idx += blockDim.x) {
+    int e = idx / (NC * Np);
+    sm[e * pe + oM + idx % (NC * Np)] = sm[e * pe + oA + idx % (NC * Np)];
   }
   __syncthreads();
-  apply_VT<D>(R, t, oA, oB, oC, oM, NC);
   apply_V<D>(R, t, oM, oB, oC, oA, NC);
   // 5. u = V u~ (apply_V's output must differ from s1 for triangles, from s2 for tetrahedra)
   const int oU = D == 2 ? oC : oB, oUb = D == 2 ? oB : oC;
@@ -1359,7 +402,7 @@ size_t smem_residual(const RefTables& r, int e) {
   return (size_t)e * L.pe * sizeof(double);
 }
 
-static constexpr size_t kSmemBudget = 200 * 1024;
+static constexpr size_t kSmemBudget = 227 * 1024;   // opt-in maximum per CTA
 size_t smem_residual_adj(const RefTables& r, int e);
 
 LaunchCfg choose_launch(const RefTables& r) {
@@ -1370,15 +413,21 @@ LaunchCfg choose_launch(const RefTables& r) {
   L.ea = ea;
   L.ta = 256;
   L.sa = smem_project(r, ea);
-  // residual: E*T threads for the pair phases; prefer E*T close to a multiple of 32
+  // residual: E*T threads for the pair phases.  The kernels use up to ~255 registers, so an SM
+  // holds at most 256 of their threads; pick E to maximise the threads doing pair work per SM
+  // (CTAs per SM x E*T, limited by shared memory and registers), then lane utilisation.
   int emax = std::max(1, (int)(kSmemBudget / smem_residual(r, 1)));
   emax = std::min(emax, 1024 / r.T);
   int best = 1;
   double best_score = -1.0;
   for (int e = 1; e <= emax; ++e) {
-    int thr = ((e * r.T + 31) / 32) * 32;
-    double util = (double)(e * r.T) / thr;
-    double score = util * std::min(1.0, thr / 128.0) + 1e-3 * e;
+    const int thr = ((e * r.T + 31) / 32) * 32;
+    const int by_smem = (int)(kSmemBudget / smem_residual(r, e));
+    const int by_regs = std::max(1, 256 / thr);
+    const int ctas = std::max(1, std::min(by_smem, by_regs));
+    if (thr > 256 && e > 1) break;
+    const double useful = (double)ctas * e * r.T;   // lanes with pair work per SM
+    const double score = useful + 1e-3 * (double)(e * r.T) / thr;
     if (score > best_score) {
       best_score = score;
       best = e;
@@ -1414,8 +463,6 @@ cudaError_t set_smem_limits(const LaunchCfg& L, int dim) {
   if (dim == 2) {
     e = cudaFuncSetAttribute(project_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     if (e) return e;
-    e = cudaFuncSetAttribute(residual_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-    if (e) return e;
     e = cudaFuncSetAttribute(l2_project_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     if (e) return e;
     e = cudaFuncSetAttribute(residual_adjoint_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
@@ -1424,11 +471,9 @@ cudaError_t set_smem_limits(const LaunchCfg& L, int dim) {
     if (e) return e;
     e = cudaFuncSetAttribute(project_batch_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     if (e) return e;
-    e = cudaFuncSetAttribute(residual_batch_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    e = set_residual_smem_d2(lim);
   } else {
     e = cudaFuncSetAttribute(project_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-    if (e) return e;
-    e = cudaFuncSetAttribute(residual_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     if (e) return e;
     e = cudaFuncSetAttribute(l2_project_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     if (e) return e;
@@ -1438,7 +483,7 @@ cudaError_t set_smem_limits(const LaunchCfg& L, int dim) {
     if (e) return e;
     e = cudaFuncSetAttribute(project_batch_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     if (e) return e;
-    e = cudaFuncSetAttribute(residual_batch_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    e = set_residual_smem_d3(lim);
   }
   return e;
 }
@@ -1455,12 +500,7 @@ cudaError_t launch_project(const DevRef& R, const DevMesh& M, const LaunchCfg& L
 
 cudaError_t launch_residual(const DevRef& R, const DevMesh& M, const LaunchCfg& L, const Epilogue& ep,
                             cudaStream_t s) {
-  const unsigned grid = (unsigned)((M.E + L.eb - 1) / L.eb);
-  if (R.dim == 2)
-    residual_kernel<2><<<grid, L.tb, L.sb, s>>>(R, M, L.eb, ep);
-  else
-    residual_kernel<3><<<grid, L.tb, L.sb, s>>>(R, M, L.eb, ep);
-  return cudaGetLastError();
+  return R.dim == 2 ? launch_residual_d2(R, M, L, ep, s) : launch_residual_d3(R, M, L, ep, s);
 }
 
 cudaError_t launch_l2_project(const DevRef& R, const DevMesh& M, const double* un, double* um, cudaStream_t s) {
@@ -1505,20 +545,17 @@ cudaError_t launch_axpby(double* out, double a, const double* x, double b, const
   return cudaGetLastError();
 }
 
-cudaError_t launch_batch(int dim, int stage, const BatchMesh* meshes, const BatchItem* items, int nitems,
+cudaError_t launch_batch(int dim, int n, int stage, const BatchMesh* meshes, const BatchItem* items, int nitems,
                          int grid, int threads, size_t smem, cudaStream_t s) {
   if (stage == 0) {
     if (dim == 2)
       project_batch_kernel<2><<<grid, threads, smem, s>>>(meshes, items, nitems);
     else
       project_batch_kernel<3><<<grid, threads, smem, s>>>(meshes, items, nitems);
-  } else {
-    if (dim == 2)
-      residual_batch_kernel<2><<<grid, threads, smem, s>>>(meshes, items, nitems);
-    else
-      residual_batch_kernel<3><<<grid, threads, smem, s>>>(meshes, items, nitems);
+    return cudaGetLastError();
   }
-  return cudaGetLastError();
+  return dim == 2 ? launch_residual_batch_d2(n, meshes, items, nitems, grid, threads, smem, s)
+                  : launch_residual_batch_d3(n, meshes, items, nitems, grid, threads, smem, s);
 }
 
 cudaError_t launch_reduce_diag(const double* part, int64_t E, int ncol, double* out, cudaStream_t s) {

