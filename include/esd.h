@@ -215,6 +215,10 @@ esd_status esd_ref_info(int dim, int p, esd_info* out);
 esd_status esd_debug_host_setup(const esd_mesh_desc* desc, double* wj, double* bj, double* nrm, double* vdir,
                                 double* fdir, int32_t* nbr, int32_t* nbr_node, double* xvol);
 
+/* Test hook: y = log(x) (which = 0) or exp(x) (which = 1) elementwise with the library's
+ * table-driven device implementations; x, y device arrays of n doubles. */
+esd_status esd_debug_math(int which, const double* x, double* y, int64_t n, void* stream);
+
 const char* esd_status_string(esd_status s);
 const char* esd_last_error(void);
 

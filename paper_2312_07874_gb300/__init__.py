@@ -66,6 +66,8 @@ SYMBOLS = {
     "esd_measure_fp64_peak": ([ctypes.POINTER(ctypes.c_double), ctypes.c_void_p], ctypes.c_int),
     "esd_ref_info": ([ctypes.c_int, ctypes.c_int, ctypes.POINTER(esd_info)], ctypes.c_int),
     "esd_debug_host_setup": ([ctypes.POINTER(esd_mesh_desc)] + [ctypes.c_void_p] * 8, ctypes.c_int),
+    "esd_debug_math": ([ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p],
+                       ctypes.c_int),
     "esd_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "esd_last_error": ([], ctypes.c_char_p),
 }
@@ -212,6 +214,10 @@ def esd_autotune(h, u, stream=None):
 def esd_launch_stage(h, stage, u=None, out=None, stream=None):
     _check(lib().esd_launch_stage(h, int(stage), _ptr(u) if u is not None else None,
                                   _ptr(out) if out is not None else None, _stream(stream)))
+
+
+def esd_debug_math(which, x, y, stream=None):
+    _check(lib().esd_debug_math(int(which), _ptr(x), _ptr(y), x.numel(), _stream(stream)))
 
 
 def esd_measure_fp64_peak(stream=None):

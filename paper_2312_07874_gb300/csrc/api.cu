@@ -144,6 +144,9 @@ esd_status esd_mesh_create(const esd_mesh_desc* d, esd_mesh* out) {
   };
   size_t o_psi1 = push(r.psi1), o_psi2 = push(r.psi2), o_psi3 = push(r.psi3), o_l1m = push(r.l1m),
          o_l1p = push(r.l1p), o_l2m = push(r.l2m), o_l3m = push(r.l3m), o_L2J = push(r.L2J), o_w = push(r.wvol);
+  std::vector<double> mt(kMathTabSize);
+  build_math_table(mt.data());
+  size_t o_mt = push(mt);
   double* dtab = nullptr;
   int* itab = nullptr;
   if ((st = m->upload(&dtab, dt)) != ESD_OK || (st = m->upload(&itab, r.ints)) != ESD_OK) {
@@ -158,6 +161,7 @@ esd_status esd_mesh_create(const esd_mesh_desc* d, esd_mesh* out) {
   R.l1m = dtab + o_l1m; R.l1p = dtab + o_l1p; R.l2m = dtab + o_l2m; R.l3m = dtab + o_l3m; R.L2J = dtab + o_L2J;
   R.wvol = dtab + o_w;
   R.dense_minv = r.dense_minv;
+  R.mtab = dtab + o_mt;
   R.off1 = itab + r.i_off1; R.s12a1 = itab + r.i_s12a1; R.moff = itab + r.i_moff; R.mode = itab + r.i_mode;
   // per-element data
   DevMesh& M = m->M;
@@ -824,6 +828,32 @@ esd_status esd_debug_host_setup(const esd_mesh_desc* d, double* wj, double* bj, 
   cp(wj, H.wj); cp(bj, H.bj); cp(nrm, H.nrm); cp(vdir, H.vdir); cp(fdir, H.fdir);
   cp(nbr, H.nbr_e); cp(nbr_node, H.nbr_f); cp(xvol, H.xvol);
   return ESD_OK;
+}
+
+esd_status esd_debug_math(int which, const double* x, double* y, int64_t n, void* stream) {
+  if (which != 0 && which != 1) return fail(ESD_ERR_ARG, "which must be 0 (log) or 1 (exp)");
+  esd_status st;
+  if ((st = check_dev(x, "x")) || (st = check_dev(y, "y"))) return st;
+  static std::mutex mu;
+  static double* tab[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return fail(ESD_ERR_UNSUPPORTED, "device index");
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (!tab[dev]) {
+      std::vector<double> h(kMathTabSize);
+      build_math_table(h.data());
+      void* p = nullptr;
+      cudaError_t e = cudaMalloc(&p, h.size() * sizeof(double));
+      if (e) return cuda_fail(e, "math table");
+      e = cudaMemcpy(p, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice);
+      if (e) return cuda_fail(e, "math table");
+      tab[dev] = static_cast<double*>(p);
+    }
+  }
+  cudaError_t e = launch_math_probe(which, tab[dev], x, y, n, (cudaStream_t)stream);
+  return e ? cuda_fail(e, "math probe") : ESD_OK;
 }
 
 esd_status esd_measure_fp64_peak(double* flops, void* stream) {

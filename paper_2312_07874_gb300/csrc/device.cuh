@@ -101,6 +101,44 @@ __device__ __forceinline__ bool below_logmean_cutoff(double u) {
   return __double_as_longlong(u) < 0x3F1A36E2EB1C432DLL;   // bit pattern of 1.0e-4
 }
 
+// Table-driven logarithm (after Tang, 1990): x = 2^k m, F = 1 + j/128 nearest to m,
+// ln x = k ln2 + ln F + log1p((m - F)/F), with log1p(r) = r + r^2 q(r) to degree 7
+// (|r| <= 2^-8).  For positive normal x; ~1 ulp.
+__device__ __forceinline__ double log_tab(double x, const double* __restrict__ T) {
+  const long long b = __double_as_longlong(x);
+  const long long k = (b >> 52) - 1023;
+  const long long mb = b & 0x000FFFFFFFFFFFFFLL;
+  const int j = (int)((mb + (1LL << 44)) >> 45);
+  const double m = __longlong_as_double(mb | 0x3FF0000000000000LL);
+  const double F = __longlong_as_double(0x3FF0000000000000LL + ((long long)j << 45));
+  const double r = (m - F) * __ldg(T + j);
+  const double r2 = r * r;
+  const double q = fma(r, fma(r, fma(r, fma(r, fma(r, 1.0 / 7.0, -1.0 / 6.0), 1.0 / 5.0), -1.0 / 4.0), 1.0 / 3.0),
+                       -0.5);
+  const double kd = __longlong_as_double(0x4338000000000000LL + k) - 6755399441055744.0;
+  const double hi = fma(kd, __ldg(T + 451), __ldg(T + 129 + j));
+  const double lo = fma(kd, __ldg(T + 452), __ldg(T + 258 + j));
+  return hi + (lo + fma(r2, q, r));
+}
+
+// Table-driven exponential (after Tang, 1989): x = (32 m + j) ln2/32 + r, |r| <= ln2/64,
+// e^x = 2^m 2^(j/32) (1 + expm1(r)), expm1 to degree 6.  For results in the normal range.
+__device__ __forceinline__ double exp_tab(double x, const double* __restrict__ T) {
+  const double magic = 6755399441055744.0;   // 1.5 * 2^52
+  const double t = fma(x, __ldg(T + 455), magic);
+  const long long n = __double_as_longlong(t) - 0x4338000000000000LL;
+  const double nd = t - magic;
+  double r = fma(-nd, __ldg(T + 453), x);
+  r = fma(-nd, __ldg(T + 454), r);
+  const int j = (int)(n & 31);
+  const long long me = n >> 5;
+  const double r2 = r * r;
+  const double p = fma(r2, fma(r, fma(r, fma(r, fma(r, 1.0 / 720.0, 1.0 / 120.0), 1.0 / 24.0), 1.0 / 6.0), 0.5), r);
+  const double s = __ldg(T + 387 + j);
+  const double res = s + fma(s, p, __ldg(T + 419 + j));
+  return __longlong_as_double(__double_as_longlong(res) + (me << 52));
+}
+
 struct FluxK {
   double inv_gm1;
   double k0, k1, k2, k3;   // (2, 2/3, 2/5, 2/7) / (gamma - 1)
@@ -380,19 +418,23 @@ __device__ __forceinline__ bool finite_pos(double x) { return x > 0.0 && x < 1.0
 
 // entropy variables W(u) = grad_U S (Section 7.1), times the weight W J
 template <int D>
-__device__ __forceinline__ void entropy_vars(const double* u, double gamma, double scale, double* w, int* bad) {
+__device__ __forceinline__ void entropy_vars(const double* u, double gamma, double scale, double* w, int* bad,
+                                             const double* __restrict__ mt) {
   double rho = u[0];
-  double ir = 1.0 / rho, vv = 0.0, v[D];
+  double ir = rcp_nr<2>(rho), vv = 0.0, v[D];
 #pragma unroll
   for (int k = 0; k < D; ++k) {
     v[k] = u[1 + k] * ir;
     vv = fma(v[k], v[k], vv);
   }
   double p = (gamma - 1.0) * (u[D + 1] - 0.5 * rho * vv);
-  if (!finite_pos(rho) || !finite_pos(p)) *bad = 1;
-  double s = log(p) - gamma * log(rho);
-  double b = rho / p;
-  w[0] = scale * ((gamma - s) / (gamma - 1.0) - 0.5 * b * vv);
+  if (!finite_pos(rho) || !finite_pos(p)) {
+    *bad = 1;
+    p = rho = 1.0;   // keep the arithmetic finite; the state is reported as non-admissible
+  }
+  double s = log_tab(p, mt) - gamma * log_tab(rho, mt);
+  double b = rho * rcp_nr<2>(p);
+  w[0] = scale * ((gamma - s) * (1.0 / (gamma - 1.0)) - 0.5 * b * vv);
 #pragma unroll
   for (int k = 0; k < D; ++k) w[1 + k] = scale * b * v[k];
   w[D + 1] = -scale * b;
@@ -402,20 +444,24 @@ __device__ __forceinline__ void entropy_vars(const double* u, double gamma, doub
 // flux state: b = -w_last = rho/p, v = w_v/b, s = gamma - (gamma-1)(w_1 + b|v|^2/2),
 // ln rho = -(s + ln b)/(gamma-1), p = rho/b.
 template <int D>
-__device__ __forceinline__ NodeState<D> state_from_entropy(const double* w, double gamma, int* bad) {
+__device__ __forceinline__ NodeState<D> state_from_entropy(const double* w, double gamma, int* bad,
+                                                           const double* __restrict__ mt) {
   NodeState<D> st;
   double b = -w[D + 1];
-  if (!finite_pos(b)) *bad = 1;
-  double ib = 1.0 / b, vv = 0.0;
+  if (!finite_pos(b)) {
+    *bad = 1;
+    b = 1.0;
+  }
+  double ib = rcp_nr<2>(b), vv = 0.0;
 #pragma unroll
   for (int k = 0; k < D; ++k) {
     st.v[k] = w[1 + k] * ib;
     vv = fma(st.v[k], st.v[k], vv);
   }
   double s = gamma - (gamma - 1.0) * (w[0] + 0.5 * b * vv);
-  double lb = log(b);
-  st.lrho = -(s + lb) / (gamma - 1.0);
-  st.rho = exp(st.lrho);
+  double lb = log_tab(b, mt);
+  st.lrho = -(s + lb) * (1.0 / (gamma - 1.0));
+  st.rho = (st.lrho > -700.0 && st.lrho < 700.0) ? exp_tab(st.lrho, mt) : exp(st.lrho);
   st.p = st.rho * ib;
   st.beta = b;
   st.lbeta = lb;
@@ -463,7 +509,7 @@ __device__ void project_tile(const DevRef& R, const DevMesh& M, int64_t e0, int 
     double* A = sm + e * pe + oA;
 #pragma unroll
     for (int c = 0; c < NC; ++c) uu[c] = A[c * Nq + v];
-    entropy_vars<D>(uu, M.gamma, M.wj[(e0 + e) * Nq + v], ww, &lbad);
+    entropy_vars<D>(uu, M.gamma, M.wj[(e0 + e) * Nq + v], ww, &lbad, R.mtab);
 #pragma unroll
     for (int c = 0; c < NC; ++c) A[c * Nq + v] = ww[c];
   }
@@ -495,7 +541,7 @@ __device__ void project_tile(const DevRef& R, const DevMesh& M, int64_t e0, int 
     const int str = k < Nq ? Nq : Nfn;
 #pragma unroll
     for (int c = 0; c < NC; ++c) ww[c] = src[c * str];
-    NodeState<D> st = state_from_entropy<D>(ww, M.gamma, &lbad);
+    NodeState<D> st = state_from_entropy<D>(ww, M.gamma, &lbad, R.mtab);
     store_state<D>(M.states + (e0 + e) * NF * Ntot, Ntot, k, st);
     if (k >= Nq) M.cfac[(e0 + e) * Nfn + (k - Nq)] = sqrt(M.gamma * st.p / st.rho);
   }

@@ -64,6 +64,14 @@ esd_status build_ref(int dim, int p, RefTables* out, std::string* err);
 esd_status build_host_mesh(const esd_mesh_desc& d, HostMesh* out, std::string* err);
 
 // Device views passed to kernels by value.
+// Tables of the table-driven logarithm and exponential (device.cuh: log_tab, exp_tab),
+// laid out in one array of doubles:
+//   [0,129) 1/F_j, [129,258) ln F_j (high part), [258,387) ln F_j (low part), F_j = 1 + j/128;
+//   [387,419) 2^(j/32) (high), [419,451) 2^(j/32) (low);
+//   [451] ln2 high, [452] ln2 low, [453] (ln2/32) high, [454] (ln2/32) low, [455] 32/ln2.
+constexpr int kMathTabSize = 456;
+void build_math_table(double* out);   // setup.cpp, host long double
+
 struct DevRef {
   int dim, p, n, Nq, Np, Nf, Nqf, Nfn, Ntot, T, Lv, S12, nvp, nfp;
   int fph_off[4], fph_len[4];
@@ -72,6 +80,7 @@ struct DevRef {
   const double *l1m, *l1p, *l2m, *l3m, *L2J;
   const double* wvol;
   int dense_minv;
+  const double* mtab;   // kMathTabSize doubles
 };
 
 struct DevMesh {
@@ -148,6 +157,7 @@ cudaError_t set_residual_smem_d3(int lim);
 cudaError_t launch_reduce_diag(const double* part, int64_t E, int ncol, double* out, cudaStream_t s);
 cudaError_t launch_copy(const double* src, double* dst, int64_t n, cudaStream_t s);
 cudaError_t measure_fp64(double* flops, cudaStream_t s);
+cudaError_t launch_math_probe(int which, const double* mtab, const double* x, double* y, int64_t n, cudaStream_t s);
 cudaError_t set_smem_limits(const LaunchCfg& L, int dim);
 
 }  // namespace esd

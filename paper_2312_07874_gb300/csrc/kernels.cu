@@ -374,6 +374,13 @@ __global__ void copy_kernel(const double* __restrict__ a, double* __restrict__ b
     b[i] = a[i];
 }
 
+// evaluates log_tab (which = 0) or exp_tab (which = 1) elementwise (accuracy tests)
+__global__ void math_probe_kernel(int which, const double* __restrict__ mt, const double* __restrict__ x,
+                                  double* __restrict__ y, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = which == 0 ? log_tab(x[i], mt) : exp_tab(x[i], mt);
+}
+
 __global__ void fp64_fma_kernel(double* out, int iters) {
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   double a[8];
@@ -565,6 +572,11 @@ cudaError_t launch_reduce_diag(const double* part, int64_t E, int ncol, double* 
 
 cudaError_t launch_copy(const double* src, double* dst, int64_t n, cudaStream_t s) {
   copy_kernel<<<152 * 4, 256, 0, s>>>(src, dst, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_math_probe(int which, const double* mtab, const double* x, double* y, int64_t n, cudaStream_t s) {
+  math_probe_kernel<<<152 * 4, 256, 0, s>>>(which, mtab, x, y, n);
   return cudaGetLastError();
 }
 

@@ -778,4 +778,43 @@ esd_status build_host_mesh(const esd_mesh_desc& d, HostMesh* H, std::string* err
   return ESD_OK;
 }
 
+// Tables of the table-driven log (after Tang, "Table-driven implementation of the
+// logarithm function in IEEE floating-point arithmetic", 1990) and exp (after Tang,
+// "Table-driven implementation of the exponential function in IEEE floating-point
+// arithmetic", 1989), computed in long double.  High parts carry trailing zeros so that
+// k * ln2_hi + (ln F)_hi and n * (ln2/32)_hi are exact in double.
+void build_math_table(double* t) {
+  auto round_to = [](long double v, int bits_after_point) {   // v rounded to a multiple of 2^-bits
+    long double s = std::ldexp(1.0L, bits_after_point);
+    return (double)(std::nearbyint(v * s) / s);
+  };
+  const long double ln2 = std::log(2.0L);
+  for (int j = 0; j <= 128; ++j) {
+    const long double F = 1.0L + j / 128.0L;
+    t[j] = (double)(1.0L / F);
+    const long double L = std::log(F);
+    const double hi = round_to(L, 42);
+    t[129 + j] = hi;
+    t[258 + j] = (double)(L - (long double)hi);
+  }
+  for (int j = 0; j < 32; ++j) {
+    const long double S = std::exp2((long double)j / 32.0L);
+    const double hi = (double)S;
+    t[387 + j] = hi;
+    t[419 + j] = (double)(S - (long double)hi);
+  }
+  const double ln2_hi = round_to(ln2, 32);
+  t[451] = ln2_hi;
+  t[452] = (double)(ln2 - (long double)ln2_hi);
+  // F_128 = 2: store ln 2 split exactly like the k ln 2 term, so that for x just below 1
+  // (k = -1, j = 128) both halves cancel exactly and only the polynomial remains.
+  t[129 + 128] = t[451];
+  t[258 + 128] = t[452];
+  const long double l32 = ln2 / 32.0L;
+  const double l32_hi = round_to(l32, 46);
+  t[453] = l32_hi;
+  t[454] = (double)(l32 - (long double)l32_hi);
+  t[455] = (double)(32.0L / ln2);
+}
+
 }  // namespace esd
