@@ -415,8 +415,8 @@ def run_reference(args):
 # ---------------------------------------------------------------------------------
 def batch_mix(seed=5, n=64):
     """Seeded mix: triangles on uniform 2D grids (2 M^2 in [200, 20000]), tetrahedra from
-    uniform cube splits (6 M^3 in [384, 24576]), p uniform in {2..10} (tetrahedra {2..6}, the
-    degrees this build supports for them), vortex or Taylor-Green states."""
+    uniform cube splits (6 M^3 in [384, 24576]), p uniform in {2..10} for both, vortex or
+    Taylor-Green states (about 110 GB of device memory in total)."""
     rng = np.random.default_rng(seed)
     mix = []
     for i in range(n):
@@ -425,7 +425,7 @@ def batch_mix(seed=5, n=64):
             mix.append((2, M, int(rng.integers(2, 11)), "vortex"))
         else:
             M = int(rng.integers(4, 17))
-            mix.append((3, M, int(rng.integers(2, 7)), "tgv"))
+            mix.append((3, M, int(rng.integers(2, 11)), "tgv"))
     return mix
 
 
@@ -480,6 +480,107 @@ def run_batch(args):
     E.esd_batch_destroy(b)
 
 
+# ---------------------------------------------------------------------------------
+# per-configuration sweep: single-residual and RK4 throughput with the residual kernel's
+# roofline fraction (not the headline line; one JSON line per configuration)
+# ---------------------------------------------------------------------------------
+SWEEP = ([("tri_vortex_curved", 2, 64, 1.0, p, "vortex") for p in (4, 6, 8, 10)]
+         + [("tet_tgv_curved", 3, 16, 2 * np.pi, p, "tgv") for p in (2, 4, 6)])
+
+
+def _time_flushed(torch, stream, fn, reps, flush):
+    """Mean device time of fn() over reps launches, L2 flushed (a 256 MB write) before each."""
+    tot = 0.0
+    with torch.cuda.stream(stream):
+        fn()
+        for _ in range(reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            stream.synchronize()
+            tot += a.elapsed_time(b)
+    return tot / reps
+
+
+def run_sweep(args):
+    import torch
+    import paper_2312_07874_gb300 as E
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(32 * 1024 * 1024, dtype=torch.float64, device=dev)
+    peak = E.esd_measure_fp64_peak(stream)
+    reps = max(3, args.steps)
+    for name, dim, M, L, p, state in SWEEP:
+        mesh, X = I.config_mesh(dim, M, L, p, True)
+        gm = E.Mesh(dim, p, X, mesh.nbr_elem, mesh.nbr_face, flux="LF")
+        f = I.config_state_fn(dim, L, state)
+        x = gm.volume_nodes()
+        nod = f(x)
+        if dim == 2:   # seeded U(-1e-3, 1e-3) on nodal density
+            nod[..., 0] += I.seeded_uniform(1, nod[..., 0].shape, -1e-3, 1e-3)
+        u = gm.l2_project(torch.from_numpy(np.ascontiguousarray(np.transpose(nod, (0, 2, 1)))).to(dev))
+        lam = I.max_wave_speed_sampled(f, dim, L)
+        dt = 0.1 * (L / M) / (lam * (2 * p + 1))
+        info = gm.info
+        nE = info["n_elem"]
+        dof = nE * info["n_modes"] * info["n_c"]
+        out = torch.empty_like(u)
+        rhs_ms = _time_flushed(torch, stream, lambda: E.esd_rhs(gm.handle, u, out, stream), reps, flush)
+        E.esd_launch_stage(gm.handle, 0, u, None, stream)
+        res_ms = _time_flushed(torch, stream, lambda: E.esd_launch_stage(gm.handle, 1, None, out, stream),
+                               reps, flush)
+        proj_ms = _time_flushed(torch, stream, lambda: E.esd_launch_stage(gm.handle, 0, u, None, stream),
+                                reps, flush)
+        ur = u.clone()
+        rk_ms = _time_flushed(torch, stream, lambda: gm.rk_step(ur, dt), reps, flush)
+        gm.check()
+        rflops, npairs = residual_kernel_flops(dim, p)
+        line = {"kind": "sweep", "workload": f"{name} p={p}", "n_elem": nE, "p": p, "dof": dof,
+                "rhs": {"ms": rhs_ms, "dof_residual_updates_per_s": dof / (rhs_ms * 1e-3),
+                        "two_point_fluxes_per_s": npairs * nE / (rhs_ms * 1e-3)},
+                "rk4_step": {"ms": rk_ms, "dof_residual_updates_per_s": 4 * dof / (rk_ms * 1e-3)},
+                "residual_kernel": {"ms": res_ms, "achieved_tflops": rflops * nE / (res_ms * 1e-3) / 1e12,
+                                    "peak_tflops": peak / 1e12, "frac": rflops * nE / (res_ms * 1e-3) / peak,
+                                    "bound": "alu", "algorithmic_flops_per_elem": rflops},
+                "project_kernel_ms": proj_ms,
+                "l2": "flushed (256 MB write) before every timed launch", "dtype": "f64"}
+        print(json.dumps(line), flush=True)
+        del gm, u, ur, out
+        torch.cuda.empty_cache()
+    # differentiation workload: VJP of esd_rhs on 3072 curved tets at p = 3, and a 20-step
+    # RK4 rollout with per-stage checkpoints through torch.autograd
+    from paper_2312_07874_gb300.autograd import rollout
+    mesh, X = I.config_mesh(3, 8, 2 * np.pi, 3, True)
+    gm = E.Mesh(3, 3, X, mesh.nbr_elem, mesh.nbr_face, flux="LF")
+    x = gm.volume_nodes()
+    nod = np.transpose(I.taylor_green(x, 0.1), (0, 2, 1))
+    u = gm.l2_project(torch.from_numpy(np.ascontiguousarray(nod)).to(dev))
+    u += torch.from_numpy(I.seeded_normal(21, tuple(u.shape), 1e-3)).to(dev)
+    cot = torch.from_numpy(I.seeded_normal(22, tuple(u.shape), 1.0)).to(dev)
+    out, grad = torch.empty_like(u), torch.empty_like(u)
+    fwd = _time_flushed(torch, stream, lambda: E.esd_rhs(gm.handle, u, out, stream), reps, flush)
+    adj = _time_flushed(torch, stream, lambda: E.esd_rhs_vjp(gm.handle, u, cot, grad, stream), reps, flush)
+    lam = I.max_wave_speed_sampled(lambda y: I.taylor_green(y, 0.1), 3, 2 * np.pi)
+    dt = 0.1 * (2 * np.pi / 8) / (lam * 7)
+
+    def fwd_only():
+        with torch.no_grad():
+            rollout(u, gm, dt, 20, "stages")
+
+    def fwd_bwd():
+        u0 = u.clone().requires_grad_(True)
+        (cot * rollout(u0, gm, dt, 20, "stages")).sum().backward()
+    t_f = _time_flushed(torch, stream, fwd_only, 2, flush)
+    t_fb = _time_flushed(torch, stream, fwd_bwd, 2, flush)
+    print(json.dumps({"kind": "sweep", "workload": "vjp tet_tgv_curved p=3 (8^3 x 6 = 3072 tets, TGV + N(0,1e-3))",
+                      "rhs_ms": fwd, "rhs_vjp_ms": adj, "adjoint_forward_ratio": adj / fwd,
+                      "rollout_20_steps_ms": t_f, "rollout_20_steps_forward_backward_ms": t_fb,
+                      "rollout_backward_forward_ratio": (t_fb - t_f) / t_f, "checkpoint": "stages",
+                      "l2": "flushed (256 MB write) before every timed call", "dtype": "f64"}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -489,10 +590,15 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="0 skips the CPU baseline")
     ap.add_argument("--mesh-m", type=int, default=16, help="cells per direction (16 = the benchmark)")
     ap.add_argument("--batch", action="store_true", help="64-mesh batched vs per-mesh comparison")
+    ap.add_argument("--sweep", action="store_true", help="per-degree throughput of the triangle and "
+                    "tetrahedron workloads and the differentiation workload (one line each)")
     args = ap.parse_args()
     WORKLOAD["M"] = args.mesh_m
     if args.batch:
         run_batch(args)
+        return
+    if args.sweep:
+        run_sweep(args)
         return
     if args.warmup < 3:
         args.warmup = 3

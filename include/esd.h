@@ -75,7 +75,7 @@ typedef struct esd_batch_s* esd_batch;
  */
 typedef struct {
   int dim;                  /* 2 (triangles) or 3 (tetrahedra) */
-  int p;                    /* polynomial degree p = q = p_g; 1..10 (triangles), 1..6 (tetrahedra) */
+  int p;                    /* polynomial degree p = q = p_g; 1..10 (triangles and tetrahedra) */
   int64_t n_elem;
   const double* map_nodes;
   const int32_t* nbr_elem;

@@ -558,6 +558,11 @@ struct ResLayout {
   int oSv, oSf, oPart, oS1, oS2, oMod, oR, oH, pe;
 };
 
+// Facet-4 columns handled per pass of the eta3 phase (tetrahedra).  The per-task partial
+// sums of a pass take N_c x n^2 x (columns) doubles; at n = 11 the full n columns would not
+// fit next to the states, so the facet-4 work runs in two passes there.
+__host__ __device__ constexpr int facet4_cols(int n) { return n > 10 ? (n + 1) / 2 : n; }
+
 template <int D>
 __host__ __device__ inline ResLayout res_layout(int Nq, int Nfn, int Np, int n) {
   constexpr int NC = D + 2, NF = D + 5;
@@ -565,7 +570,7 @@ __host__ __device__ inline ResLayout res_layout(int Nq, int Nfn, int Np, int n) 
   L.oSv = 0;
   L.oSf = NF * Nq;
   L.oPart = L.oSf + NF * Nfn;
-  int r0 = L.oPart + (D == 3 ? NC * n * n * n : 0);
+  int r0 = L.oPart + (D == 3 ? NC * n * n * facet4_cols(n) : 0);
   L.oS1 = 0;
   L.oS2 = NC * Nq;
   L.oMod = 2 * NC * Nq;
@@ -590,11 +595,13 @@ __device__ __forceinline__ void load_dir(const double* base, int slot, int T, in
 //   tetrahedra: phase 0 = eta1-lines + facets 2, 3; phase 1 = eta2-lines + facet 1;
 //               phase 2 = eta3-lines + facet-4 pairs (per-task partial sums);
 //   triangles:  phase 0 = eta1-lines + facets 2, 3; phase 1 = eta2-lines + facet 1.
+//   In phase 2 the facet-4 columns b' in [b0, b1) are handled (partials stored at column
+//   b' - b0); the eta3-line volume pairs only with b0 == 0.
 template <int D, int N>
 __device__ __forceinline__ void line_task(int ph, int t, const DevRef& R, const double* __restrict__ Sv,
                                           const double* __restrict__ Sf, double* r, double* h, double* part,
                                           const double* __restrict__ vdir, const double* __restrict__ fdir,
-                                          const FluxK& K) {
+                                          const FluxK& K, int b0 = 0, int b1 = N) {
   constexpr int NC = D + 2;
   const int Nq = R.Nq, Nfn = R.Nfn, Nqf = R.Nqf, T = R.T;
   int base, stride;
@@ -613,20 +620,22 @@ __device__ __forceinline__ void line_task(int ph, int t, const DevRef& R, const 
     for (int c = 0; c < NC; ++c) acc[a][c] = 0.0;
   constexpr int Lv = N * (N - 1) / 2;
   const double* vd = vdir + (size_t)ph * Lv * D * T + t;
+  if (b0 == 0) {
 #pragma unroll
-  for (int a = 0, m = 0; a < N; ++a) {
+    for (int a = 0, m = 0; a < N; ++a) {
 #pragma unroll
-    for (int b = a + 1; b < N; ++b, ++m) {
-      const NodeState<D> Si = load_state<D>(Sv, Nq, base + a * stride);
-      const NodeState<D> Sj = load_state<D>(Sv, Nq, base + b * stride);
-      double nh[D], F[NC];
+      for (int b = a + 1; b < N; ++b, ++m) {
+        const NodeState<D> Si = load_state<D>(Sv, Nq, base + a * stride);
+        const NodeState<D> Sj = load_state<D>(Sv, Nq, base + b * stride);
+        double nh[D], F[NC];
 #pragma unroll
-      for (int k = 0; k < D; ++k) nh[k] = vd[(m * D + k) * T];
-      ec_flux_fast<D>(Si, Sj, nh, K, F);
+        for (int k = 0; k < D; ++k) nh[k] = vd[(m * D + k) * T];
+        ec_flux_fast<D>(Si, Sj, nh, K, F);
 #pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        acc[a][c] -= F[c];
-        acc[b][c] += F[c];
+        for (int c = 0; c < NC; ++c) {
+          acc[a][c] -= F[c];
+          acc[b][c] += F[c];
+        }
       }
     }
   }
@@ -681,8 +690,9 @@ __device__ __forceinline__ void line_task(int ph, int t, const DevRef& R, const 
     // facet 4: nodes (a1, b') with a1 = t % N, against the eta3-line (a1, a2 = t / N)
     const double* fd = fdir + R.fph_off[3] + t;
     const int a1 = t % N;
+    constexpr int NB = facet4_cols(N);
 #pragma unroll 1
-    for (int bp = 0; bp < N; ++bp) {
+    for (int bp = b0; bp < b1; ++bp) {
       const int f = 3 * Nqf + a1 + N * bp;
       const NodeState<D> Sj = load_state<D>(Sf, Nfn, f);
       double hs[NC];
@@ -702,7 +712,7 @@ __device__ __forceinline__ void line_task(int ph, int t, const DevRef& R, const 
         }
       }
 #pragma unroll
-      for (int c = 0; c < NC; ++c) part[(c * T + t) * N + bp] = hs[c];
+      for (int c = 0; c < NC; ++c) part[(c * T + t) * NB + (bp - b0)] = hs[c];
     }
   }
 #pragma unroll
@@ -783,23 +793,39 @@ __device__ void residual_tile(const DevRef& R, const DevMesh& M, int64_t e0, int
     const int64_t eg = e0 + el;
     const double* vdir = active ? M.vdir + eg * (int64_t)R.nvp * D : nullptr;
     const double* fdir = active ? M.fdir + eg * (int64_t)R.nfp * D : nullptr;
-    for (int ph = 0; ph < D; ++ph) {
+    for (int ph = 0; ph < D - 1; ++ph) {
       if (active)
         line_task<D, N>(ph, t, R, sm + el * pe + Ly.oSv, sm + el * pe + Ly.oSf, sm + el * pe + Ly.oR,
                         sm + el * pe + Ly.oH, sm + el * pe + Ly.oPart, vdir, fdir, K);
       __syncthreads();
     }
-  }
-  if (D == 3) {
-    for (int idx = threadIdx.x; idx < E * NC * Nqf; idx += blockDim.x) {
-      int e = idx / (NC * Nqf), rr = idx % (NC * Nqf), c = rr / Nqf, j = rr % Nqf;
-      int a = j % n, bp = j / n;
-      const double* pp = sm + e * pe + Ly.oPart + c * T * n;
-      double s = 0.0;
-      for (int b2 = 0; b2 < n; ++b2) s += pp[(a + n * b2) * n + bp];
-      sm[e * pe + Ly.oH + c * Nfn + 3 * Nqf + j] -= s;
+    if (D == 2) {
+      if (active)
+        line_task<D, N>(1, t, R, sm + el * pe + Ly.oSv, sm + el * pe + Ly.oSf, sm + el * pe + Ly.oR,
+                        sm + el * pe + Ly.oH, sm + el * pe + Ly.oPart, vdir, fdir, K);
+      __syncthreads();
+    } else {
+      // eta3 lines and facet 4, in passes over the facet-4 columns; after each pass the
+      // per-task partials are summed over a2 into h
+      constexpr int NB = facet4_cols(N);
+      for (int b0 = 0; b0 < N; b0 += NB) {
+        const int b1 = b0 + NB < N ? b0 + NB : N;
+        if (active)
+          line_task<D, N>(2, t, R, sm + el * pe + Ly.oSv, sm + el * pe + Ly.oSf, sm + el * pe + Ly.oR,
+                          sm + el * pe + Ly.oH, sm + el * pe + Ly.oPart, vdir, fdir, K, b0, b1);
+        __syncthreads();
+        const int nb = b1 - b0;
+        for (int idx = threadIdx.x; idx < E * NC * n * nb; idx += blockDim.x) {
+          int e = idx / (NC * n * nb), rr = idx % (NC * n * nb), c = rr / (n * nb), j = rr % (n * nb);
+          int a = j % n, bq = j / n;
+          const double* pp = sm + e * pe + Ly.oPart + c * T * NB;
+          double s = 0.0;
+          for (int b2 = 0; b2 < n; ++b2) s += pp[(a + n * b2) * NB + bq];
+          sm[e * pe + Ly.oH + c * Nfn + 3 * Nqf + a + n * (b0 + bq)] -= s;
+        }
+        __syncthreads();
+      }
     }
-    __syncthreads();
   }
   // 4. lift: r -= sum_zeta R^T h  (h = B J f* - C^T 1)
   if (D == 3) {
@@ -1123,7 +1149,15 @@ __device__ void apply_RT(const DevRef& R, const Tile& t, int in, int y, int out,
 // neighbour's state through this element's interface flux (qext [E][NQ][Nfn]).
 struct AdjLayout {
   int oReg, oM, oS1, oS2, oSv, oSf, oRb, oHb, oQv, oQf, oPart, pe;
+  int glob;   // 1: q_b accumulated in the global output instead of shared memory
+  int ncol;   // facet-4 columns per pass of the partial sums
 };
+
+// Shared memory per element of the residual adjoint.  The per-node cotangents q_b are
+// accumulated in shared memory when everything fits in one CTA's 227 KB; otherwise
+// (tetrahedra of degree >= 9) they are accumulated in place in the global output q_b
+// (`glob`), and the facet-4 partials run in passes of facet4_cols(n) columns.
+constexpr int kAdjSmemBudget = 227 * 1024;
 
 template <int D>
 __host__ __device__ inline AdjLayout adj_layout(int Nq, int Nfn, int Np, int n) {
@@ -1142,7 +1176,16 @@ __host__ __device__ inline AdjLayout adj_layout(int Nq, int Nfn, int Np, int n) 
   L.oQv = L.oHb + NC * Nfn;
   L.oQf = L.oQv + NQ * Nq;
   L.oPart = L.oQf + NQ * Nfn;
+  L.ncol = n;
   L.pe = L.oPart + (D == 3 ? NQ * n * n * n : 0);
+  L.glob = 0;
+  if ((long long)L.pe * 8 > kAdjSmemBudget) {
+    L.glob = 1;
+    L.oQv = L.oQf = -1;
+    L.oPart = L.oHb + NC * Nfn;
+    L.ncol = facet4_cols(n);
+    L.pe = L.oPart + (D == 3 ? NQ * n * n * L.ncol : 0);
+  }
   return L;
 }
 

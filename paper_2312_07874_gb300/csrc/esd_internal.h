@@ -13,7 +13,7 @@
 namespace esd {
 
 constexpr int kMaxPTri = 10;
-constexpr int kMaxPTet = 6;
+constexpr int kMaxPTet = 10;
 
 // Number of per-node fields kept for the two-point flux: rho, v_1..v_d, p,
 // beta = rho/p, ln rho, ln beta.
@@ -154,6 +154,12 @@ cudaError_t launch_residual_batch_d3(int n, const BatchMesh* meshes, const Batch
                                      int threads, size_t smem, cudaStream_t s);
 cudaError_t set_residual_smem_d2(int lim);
 cudaError_t set_residual_smem_d3(int lim);
+// tetrahedra of degree 7..10 (residual_d3_hi.cu); reached through the *_d3 entry points
+cudaError_t launch_residual_d3_hi(const DevRef& R, const DevMesh& M, const LaunchCfg& L, const Epilogue& ep,
+                                  cudaStream_t s);
+cudaError_t launch_residual_batch_d3_hi(int n, const BatchMesh* meshes, const BatchItem* items, int nitems,
+                                        int grid, int threads, size_t smem, cudaStream_t s);
+cudaError_t set_residual_smem_d3_hi(int lim);
 cudaError_t launch_reduce_diag(const double* part, int64_t E, int ncol, double* out, cudaStream_t s);
 cudaError_t launch_copy(const double* src, double* dst, int64_t n, cudaStream_t s);
 cudaError_t measure_fp64(double* flops, cudaStream_t s);

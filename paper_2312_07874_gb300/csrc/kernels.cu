@@ -74,7 +74,7 @@ __global__ void l2_project_kernel(DevRef R, DevMesh M, int epc, const double* __
 
 template <int D>
 __global__ void residual_adjoint_kernel(DevRef R, DevMesh M, int epc, const double* __restrict__ cot,
-                                        double* __restrict__ qbar, double* __restrict__ qext) {
+                                        double* qbar, double* __restrict__ qext) {
   extern __shared__ double sm[];
   constexpr int NC = D + 2, NF = D + 5, NQ = D + 2;
   const int n = R.n, Nq = R.Nq, Nfn = R.Nfn, Ntot = R.Ntot, Np = R.Np, T = R.T, Nqf = R.Nqf;
@@ -112,9 +112,17 @@ __global__ void residual_adjoint_kernel(DevRef R, DevMesh M, int epc, const doub
     else
       sm[e * pe + Ly.oSf + f * Nfn + (k - Nq)] = val;
   }
+  // q_b of element e: volume node v of variable c at qv_e[c * qvs + v], facet node f at
+  // qf_e[c * qfs + f] (shared memory, or the global output itself when it does not fit)
+  const int qvs = Ly.glob ? Ntot : Nq, qfs = Ly.glob ? Ntot : Nfn;
+  auto qv_of = [&](int e) { return Ly.glob ? qbar + (e0 + e) * NQ * Ntot : sm + e * pe + Ly.oQv; };
+  auto qf_of = [&](int e) { return Ly.glob ? qbar + (e0 + e) * NQ * Ntot + Nq : sm + e * pe + Ly.oQf; };
   for (int idx = threadIdx.x; idx < E * NQ * Ntot; idx += blockDim.x) {
     int e = idx / (NQ * Ntot);
-    sm[e * pe + Ly.oQv + idx % (NQ * Ntot)] = 0.0;   // qv and qf are contiguous
+    if (Ly.glob)
+      qbar[e0 * NQ * Ntot + idx] = 0.0;
+    else
+      sm[e * pe + Ly.oQv + idx % (NQ * Ntot)] = 0.0;   // qv and qf are contiguous
   }
   __syncthreads();
   // 4. interface flux adjoint: f*_b = B J h_b
@@ -139,7 +147,7 @@ __global__ void residual_adjoint_kernel(DevRef R, DevMesh M, int epc, const doub
     iface_adj<D>(L, Rr, nn, inv_gm1, M.cfac[eg * Nfn + f], M.cfac[e2 * Nfn + f2], M.lf, fb, qL, qR);
 #pragma unroll
     for (int c = 0; c < NQ; ++c) {
-      sm[e * pe + Ly.oQf + c * Nfn + f] = qL[c];
+      qf_of(e)[c * qfs + f] = qL[c];
       qext[(eg * NQ + c) * Nfn + f] = qR[c];
     }
   }
@@ -155,8 +163,8 @@ __global__ void residual_adjoint_kernel(DevRef R, DevMesh M, int epc, const doub
   const double* Sf = sm + el * pe + Ly.oSf;
   const double* rb = sm + el * pe + Ly.oRb;
   const double* hb = sm + el * pe + Ly.oHb;
-  double* qv = sm + el * pe + Ly.oQv;
-  double* qf = sm + el * pe + Ly.oQf;
+  double* qv = active ? qv_of(el) : nullptr;
+  double* qf = active ? qf_of(el) : nullptr;
   for (int ph = 0; ph < D; ++ph) {
     if (active) {
       int base, stride;
@@ -186,8 +194,8 @@ __global__ void residual_adjoint_kernel(DevRef R, DevMesh M, int epc, const doub
           ec_flux_adj<D>(Si, Sj, nn, inv_gm1, Fb, qa, qb);
 #pragma unroll
           for (int c = 0; c < NQ; ++c) {
-            qv[c * Nq + vi] += qa[c];
-            qv[c * Nq + vj] += qb[c];
+            qv[c * qvs + vi] += qa[c];
+            qv[c * qvs + vj] += qb[c];
           }
         }
       }
@@ -208,10 +216,10 @@ __global__ void residual_adjoint_kernel(DevRef R, DevMesh M, int epc, const doub
           }
           ec_flux_adj<D>(Si, Sfj, nn, inv_gm1, Fb, qa, acc);
 #pragma unroll
-          for (int c = 0; c < NQ; ++c) qv[c * Nq + vi] += qa[c];
+          for (int c = 0; c < NQ; ++c) qv[c * qvs + vi] += qa[c];
         }
 #pragma unroll
-        for (int c = 0; c < NQ; ++c) qf[c * Nfn + f] += acc[c];
+        for (int c = 0; c < NQ; ++c) qf[c * qfs + f] += acc[c];
       };
       if (ph == 0) {
         facet_pairs(fdir + R.fph_off[0], 0, 1 * Nqf + t, n);
@@ -222,13 +230,16 @@ __global__ void residual_adjoint_kernel(DevRef R, DevMesh M, int epc, const doub
     }
     __syncthreads();
   }
-  if (D == 3) {
+  // facet 4, in passes over the facet-4 columns b' (all of them in one pass unless the
+  // partials do not fit)
+  for (int b0 = 0; D == 3 && b0 < n; b0 += Ly.ncol) {
+    const int b1 = b0 + Ly.ncol < n ? b0 + Ly.ncol : n, NB = Ly.ncol;
     double* part = sm + el * pe + Ly.oPart;
     if (active) {
       const int a = t % n, b2 = t / n;
       const double* fd = fdir + R.fph_off[3];
-      int m = 0;
-      for (int bp = 0; bp < n; ++bp) {
+      for (int bp = b0; bp < b1; ++bp) {
+        int m = bp * n;
         const int f = 3 * Nqf + a + n * bp;
         NodeState<D> Sfj = load_state<D>(Sf, Nfn, f);
         double acc[NQ];
@@ -246,24 +257,26 @@ __global__ void residual_adjoint_kernel(DevRef R, DevMesh M, int epc, const doub
           }
           ec_flux_adj<D>(Si, Sfj, nn, inv_gm1, Fb, qa, acc);
 #pragma unroll
-          for (int c = 0; c < NQ; ++c) qv[c * Nq + vi] += qa[c];
+          for (int c = 0; c < NQ; ++c) qv[c * qvs + vi] += qa[c];
         }
 #pragma unroll
-        for (int c = 0; c < NQ; ++c) part[(c * T + t) * n + bp] = acc[c];
+        for (int c = 0; c < NQ; ++c) part[(c * T + t) * NB + (bp - b0)] = acc[c];
       }
     }
     __syncthreads();
-    for (int idx = threadIdx.x; idx < E * NQ * Nqf; idx += blockDim.x) {
-      int e = idx / (NQ * Nqf), rr = idx % (NQ * Nqf), c = rr / Nqf, j = rr % Nqf;
-      int a = j % n, bp = j / n;
-      const double* pp = sm + e * pe + Ly.oPart + c * T * n;
+    const int nb = b1 - b0;
+    for (int idx = threadIdx.x; idx < E * NQ * n * nb; idx += blockDim.x) {
+      int e = idx / (NQ * n * nb), rr = idx % (NQ * n * nb), c = rr / (n * nb), j = rr % (n * nb);
+      int a = j % n, bq = j / n;
+      const double* pp = sm + e * pe + Ly.oPart + c * T * NB;
       double s = 0.0;
-      for (int b2 = 0; b2 < n; ++b2) s += pp[(a + n * b2) * n + bp];
-      sm[e * pe + Ly.oQf + c * Nfn + 3 * Nqf + j] += s;
+      for (int b2 = 0; b2 < n; ++b2) s += pp[(a + n * b2) * NB + bq];
+      qf_of(e)[c * qfs + 3 * Nqf + a + n * (b0 + bq)] += s;
     }
     __syncthreads();
   }
-  // 6. store q cotangents
+  // 6. store q cotangents (already in place when accumulated in global memory)
+  if (Ly.glob) return;
   for (int idx = threadIdx.x; idx < E * NQ * Ntot; idx += blockDim.x) {
     int e = idx / (NQ * Ntot), r = idx % (NQ * Ntot), c = r / Ntot, k = r % Ntot;
     double val = k < Nq ? sm[e * pe + Ly.oQv + c * Nq + k] : sm[e * pe + Ly.oQf + c * Nfn + (k - Nq)];

@@ -5,7 +5,7 @@ import pytest
 pytestmark = pytest.mark.gpu
 
 MIX = [(2, 3, 2, "vortex"), (2, 4, 4, "vortex"), (3, 3, 2, "tgv"), (2, 3, 7, "vortex"), (3, 3, 3, "density_wave"),
-       (3, 4, 1, "tgv")]
+       (3, 4, 1, "tgv"), (3, 3, 9, "tgv"), (3, 3, 3, "tgv")]
 
 
 def _meshes():
@@ -47,7 +47,9 @@ def test_batch_rk_step_equals_per_mesh():
     ms = _meshes()
     ua = [u.clone() for _, u in ms]
     ub = [u.clone() for _, u in ms]
-    dts = [1e-3 * (1 + k) for k in range(len(ms))]
+    # a stable step for each mesh: CFL 0.1 (h / (lambda (2p+1))), varied per mesh
+    dts = [0.1 * (2 * np.pi / M) / (12.0 * (2 * p + 1)) * (1 + 0.1 * k)
+           for k, (_, M, p, _) in enumerate(MIX)]
     b = E.esd_batch_create([m.handle for m, _ in ms])
     s = torch.cuda.Stream()
     with torch.cuda.stream(s):

@@ -55,8 +55,11 @@ def test_vjp_per_element_jacobian_transpose(dim, M, p, state):
 # traces, which nearly coincide for a smooth state: those kinks lie within ~1e-6 of the
 # state, so a difference with h = 1e-6 straddles them (error ~h, also for the oracle);
 # h = 1e-7 stays on one side.  Both use Richardson extrapolation of h and 2h.
+# Tetrahedra of degree 9 and 10 accumulate the per-node cotangents in global memory
+# (their shared-memory footprint exceeds one CTA); the same check covers that path.
 FD_CASES = [(2, 4, 3, "vortex", "EC", 1e-6), (3, 3, 3, "tgv", "EC", 1e-6),
-            (2, 4, 3, "vortex", "LF", 1e-7), (3, 3, 3, "tgv", "LF", 1e-7)]
+            (2, 4, 3, "vortex", "LF", 1e-7), (3, 3, 3, "tgv", "LF", 1e-7),
+            (3, 3, 8, "tgv", "EC", 1e-6), (3, 3, 9, "tgv", "EC", 1e-6), (3, 3, 10, "density_wave", "EC", 1e-6)]
 
 
 @pytest.mark.parametrize("dim,M,p,state,flux,h", FD_CASES)
