@@ -185,7 +185,8 @@ esd_status esd_batch_rk_step(esd_batch batch, double* const* u, const double* dt
  * threads-per-CTA and the residual kernel over elements-per-CTA on this mesh and state u
  * (device, [n_elem][N_c][N_p*], admissible), keep the fastest, and drop captured RK4
  * graphs.  Per-element arithmetic is independent of the tiling, so results are unchanged.
- * Synchronous.  Batches built afterwards use the tuned tiles. */
+ * Synchronous.  Batches built afterwards use the tuned tiles.  With the environment
+ * variable ESD_AUTOTUNE_VERBOSE=1 every candidate's time is printed to stderr. */
 esd_status esd_autotune(esd_mesh mesh, const double* u, void* stream);
 
 /* Measurement hook: launch one kernel of the esd_rhs pipeline alone, so that it can be

@@ -2,6 +2,7 @@
 // allocation at mesh creation, launch sequencing, and CUDA-graph replay of RK4.
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <functional>
 #include <mutex>
@@ -724,6 +725,8 @@ esd_status esd_autotune(esd_mesh m, const double* u, void* stream) {
   const RefTables& r = m->ref;
   const size_t budget = 227 * 1024;
   LaunchCfg best = m->L;
+  const char* ev = std::getenv("ESD_AUTOTUNE_VERBOSE");   // print every candidate's time
+  const bool verbose = ev && ev[0] == '1';
   // projection: elements per CTA x threads
   {
     float tbest = 1e30f;
@@ -735,6 +738,7 @@ esd_status esd_autotune(esd_mesh m, const double* u, void* stream) {
         L.ta = thr;
         L.sa = smem_project(r, e);
         float t = time_launches([&] { return launch_project(m->R, m->M, L, u, nullptr, s); }, s, 3);
+        if (verbose) std::fprintf(stderr, "esd_autotune: project  elems/CTA %3d threads %4d  %.4f ms\n", e, thr, t);
         if (t < tbest) {
           tbest = t;
           best.ea = L.ea;
@@ -753,13 +757,14 @@ esd_status esd_autotune(esd_mesh m, const double* u, void* stream) {
     ep.mode = 0;
     ep.dudt = m->ws_adj[0];
     float tbest = 1e30f;
-    const int emax = std::min(std::max(1, (int)(budget / smem_residual(r, 1))), std::max(1, 512 / r.T));
+    const int emax = std::min(std::max(1, (int)(budget / smem_residual(r, 1))), std::max(1, 1024 / r.T));
     for (int e = 1; e <= emax; ++e) {
       LaunchCfg L = best;
       L.eb = e;
       L.tb = std::max(64, ((e * r.T + 31) / 32) * 32);
       L.sb = smem_residual(r, e);
       float t = time_launches([&] { return launch_residual(m->R, m->M, L, ep, s); }, s, 3);
+      if (verbose) std::fprintf(stderr, "esd_autotune: residual elems/CTA %3d threads %4d  %.4f ms\n", e, L.tb, t);
       if (t < tbest) {
         tbest = t;
         best.eb = L.eb;
