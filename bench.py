@@ -337,7 +337,8 @@ def run_ours(args):
 def _kernel_hash():
     import hashlib
     h = hashlib.sha256()
-    for f in ("device.cuh", "residual_inst.cuh", "residual_d3.cu", "kernels.cu", "esd_internal.h"):
+    # sources of residual_kernel<3, N> (the adjoint and projection kernels live elsewhere)
+    for f in ("device.cuh", "residual_inst.cuh", "residual_d3.cu", "esd_internal.h"):
         h.update(open(os.path.join(ROOT, "paper_2312_07874_gb300", "csrc", f), "rb").read())
     return h.hexdigest()
 

@@ -182,7 +182,8 @@ esd_status esd_batch_rhs(esd_batch batch, const double* const* u, double* const*
 esd_status esd_batch_rk_step(esd_batch batch, double* const* u, const double* dt, void* stream);
 
 /* Autotuner (not in the paper): time the projection kernel over elements-per-CTA x
- * threads-per-CTA and the residual kernel over elements-per-CTA on this mesh and state u
+ * threads-per-CTA, and the residual kernel and the residual adjoint (esd_rhs_vjp) over
+ * elements-per-CTA, on this mesh and state u
  * (device, [n_elem][N_c][N_p*], admissible), keep the fastest, and drop captured RK4
  * graphs.  Per-element arithmetic is independent of the tiling, so results are unchanged.
  * Synchronous.  Batches built afterwards use the tuned tiles.  With the environment

@@ -773,6 +773,27 @@ esd_status esd_autotune(esd_mesh m, const double* u, void* stream) {
       }
     }
   }
+  // residual adjoint (esd_rhs_vjp): elements per CTA
+  {
+    float tbest = 1e30f;
+    const int emax = std::min(std::max(1, (int)(budget / smem_residual_adj(r, 1))), std::max(1, 1024 / r.T));
+    for (int e = 1; e <= emax; ++e) {
+      LaunchCfg L = best;
+      L.ev = e;
+      L.tv = std::max(64, ((e * r.T + 31) / 32) * 32);
+      L.sv = smem_residual_adj(r, e);
+      float t = time_launches([&] {
+        return launch_vjp(m->R, m->M, L, u, m->ws_adj[0], m->ws_adj[1], m->ws_qbar, m->ws_qext, s);
+      }, s, 2);
+      if (verbose) std::fprintf(stderr, "esd_autotune: vjp      elems/CTA %3d threads %4d  %.4f ms\n", e, L.tv, t);
+      if (t < tbest) {
+        tbest = t;
+        best.ev = L.ev;
+        best.tv = L.tv;
+        best.sv = L.sv;
+      }
+    }
+  }
   cudaError_t e = cudaStreamSynchronize(s);
   cudaGetLastError();
   if (e) return cuda_fail(e, "autotune");

@@ -129,6 +129,7 @@ struct BatchItem {
 LaunchCfg choose_launch(const RefTables& r);
 size_t smem_project(const RefTables& r, int e);
 size_t smem_residual(const RefTables& r, int e);
+size_t smem_residual_adj(const RefTables& r, int e);
 
 // Kernel launchers (kernels.cu).  All return cudaGetLastError().
 cudaError_t launch_project(const DevRef& R, const DevMesh& M, const LaunchCfg& L, const double* u,

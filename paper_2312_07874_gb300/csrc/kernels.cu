@@ -18,7 +18,7 @@
 #include <cstdio>
 #include <algorithm>
 
-#include "device.cuh"
+#include "adjoint.cuh"
 
 namespace esd {
 
