@@ -274,6 +274,10 @@ struct AdjLayout {
 // (`glob`), and the facet-4 partials run in passes of facet4_cols(n) columns.
 constexpr int kAdjSmemBudget = 227 * 1024;
 
+// Facet-4 columns per pass of the adjoint's facet-4 partial sums: all n of them, or half
+// at n = 11 where the full set would not fit next to the states.
+__host__ __device__ constexpr int facet4_cols(int n) { return n > 10 ? (n + 1) / 2 : n; }
+
 template <int D>
 __host__ __device__ inline AdjLayout adj_layout(int Nq, int Nfn, int Np, int n) {
   constexpr int NC = D + 2, NF = D + 5, NQ = D + 2;

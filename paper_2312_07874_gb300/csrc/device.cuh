@@ -551,17 +551,12 @@ __device__ void project_tile(const DevRef& R, const DevMesh& M, int64_t e0, int 
 // ---------------------------------------------------------------------------
 // Residual kernel
 // shared layout per element (doubles):
-//   region0 : states Sv[NF*Nq] | Sf[NF*Nfn] | part[NC*n^3] (tets)  -- reused as scratch later
-//   r[NC*Nq] | h[NC*Nfn]
+//   states Sv[NF*Nq] | Sf[NF*Nfn]   (reused as transform scratch S1, S2, Mod afterwards)
+//   r[NC*Nq] | h4[NC*n^2] (tetrahedra: facet-4 node accumulators)
 // ---------------------------------------------------------------------------
 struct ResLayout {
-  int oSv, oSf, oPart, oS1, oS2, oMod, oR, oH, pe;
+  int oSv, oSf, oS1, oS2, oMod, oR, oH4, pe;
 };
-
-// Facet-4 columns handled per pass of the eta3 phase (tetrahedra).  The per-task partial
-// sums of a pass take N_c x n^2 x (columns) doubles; at n = 11 the full n columns would not
-// fit next to the states, so the facet-4 work runs in two passes there.
-__host__ __device__ constexpr int facet4_cols(int n) { return n > 10 ? (n + 1) / 2 : n; }
 
 template <int D>
 __host__ __device__ inline ResLayout res_layout(int Nq, int Nfn, int Np, int n) {
@@ -569,34 +564,99 @@ __host__ __device__ inline ResLayout res_layout(int Nq, int Nfn, int Np, int n) 
   ResLayout L;
   L.oSv = 0;
   L.oSf = NF * Nq;
-  L.oPart = L.oSf + NF * Nfn;
-  int r0 = L.oPart + (D == 3 ? NC * n * n * facet4_cols(n) : 0);
+  int r0 = L.oSf + NF * Nfn;
   L.oS1 = 0;
   L.oS2 = NC * Nq;
   L.oMod = 2 * NC * Nq;
-  int r0b = L.oMod + NC * Np;
+  const int r0b = L.oMod + NC * Np;
   if (r0b > r0) r0 = r0b;
   L.oR = r0;
-  L.oH = L.oR + NC * Nq;
-  L.pe = L.oH + NC * Nfn;
+  L.oH4 = L.oR + NC * Nq;
+  L.pe = L.oH4 + (D == 3 ? NC * n * n : 0);
   return L;
 }
 
-// Pair work of one line task (Section 5.1, along collapsed-coordinate lines, Remark 4).
-// Task t of phase ph owns one eta_{ph+1}-line of N nodes and the facet nodes attached to
-// it; accumulators live in registers and the unrolled pairs are independent.
-//   tetrahedra: phase 0 = eta1-lines + facets 2, 3; phase 1 = eta2-lines + facet 1;
-//               phase 2 = eta3-lines + facet-4 pairs (per-task partial sums);
-//   triangles:  phase 0 = eta1-lines + facets 2, 3; phase 1 = eta2-lines + facet 1.
-//   In phase 2 the facet-4 columns b' in [b0, b1) are handled (partials stored at column
-//   b' - b0); the eta3-line volume pairs only with b0 == 0.
+// F = B J f* at facet node f of element eg (Eq. (interface_flux), Eq. (num_flux),
+// Eq. (wave_speed)): own trace from shared memory, the neighbour's from its stored states.
+template <int D>
+__device__ __forceinline__ void interface_flux(const DevMesh& M, int Nq, int Nfn, int Ntot, int64_t eg, int f,
+                                               const double* __restrict__ Sf, const FluxK& K, double* F) {
+  constexpr int NF = D + 5;
+  const NodeState<D> L = load_state<D>(Sf, Nfn, f);
+  const int64_t e2 = M.nbr_e[eg * Nfn + f];
+  const int f2 = M.nbr_f[eg * Nfn + f];
+  const NodeState<D> Rr = load_state<D>(M.states + e2 * NF * Ntot + Nq, Ntot, f2);
+  double nn[D], nh[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    nn[k] = M.nrm[(eg * D + k) * Nfn + f];
+    nh[k] = 0.5 * nn[k];
+  }
+  ec_flux_fast<D>(L, Rr, nh, K, F);
+  if (M.lf) {
+    double vnL = 0.0, vnR = 0.0, vvL = 0.0, vvR = 0.0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      vnL = fma(L.v[k], nn[k], vnL);
+      vnR = fma(Rr.v[k], nn[k], vnR);
+      vvL = fma(L.v[k], L.v[k], vvL);
+      vvR = fma(Rr.v[k], Rr.v[k], vvR);
+    }
+    const double lam = fmax(fabs(vnL), fabs(vnR)) + fmax(M.cfac[eg * Nfn + f], M.cfac[e2 * Nfn + f2]);
+    const double hl = 0.5 * lam;
+    F[0] -= hl * (Rr.rho - L.rho);
+#pragma unroll
+    for (int k = 0; k < D; ++k) F[1 + k] -= hl * (Rr.rho * Rr.v[k] - L.rho * L.v[k]);
+    const double EL = L.p * K.inv_gm1 + 0.5 * L.rho * vvL, ER = Rr.p * K.inv_gm1 + 0.5 * Rr.rho * vvR;
+    F[D + 1] -= hl * (ER - EL);
+  }
+  const double bj = M.bj[eg * Nfn + f];
+#pragma unroll
+  for (int c = 0; c < D + 2; ++c) F[c] *= bj;
+}
+
+// N facet-correction pairs between facet node f (state Sj) and the line's volume nodes,
+// directions fd[(a * D + k) * T]: acc[a] -= F_a, hs -= F_a.
 template <int D, int N>
-__device__ __forceinline__ void line_task(int ph, int t, const DevRef& R, const double* __restrict__ Sv,
-                                          const double* __restrict__ Sf, double* r, double* h, double* part,
-                                          const double* __restrict__ vdir, const double* __restrict__ fdir,
-                                          const FluxK& K, int b0 = 0, int b1 = N) {
+__device__ __forceinline__ void facet_strip(const double* __restrict__ Sv, int Nq, int base, int stride,
+                                            const NodeState<D>& Sj, const double* __restrict__ fd, int T,
+                                            const FluxK& K, double (&acc)[N][D + 2], double* hs) {
+#pragma unroll
+  for (int a = 0; a < N; ++a) {
+    const NodeState<D> Si = load_state<D>(Sv, Nq, base + a * stride);
+    double nh[D], F[D + 2];
+#pragma unroll
+    for (int k = 0; k < D; ++k) nh[k] = fd[(a * D + k) * T];
+    ec_flux_fast<D>(Si, Sj, nh, K, F);
+#pragma unroll
+    for (int c = 0; c < D + 2; ++c) {
+      acc[a][c] -= F[c];
+      hs[c] -= F[c];
+    }
+  }
+}
+
+// Line task t of phase ph (Section 5.1, along collapsed-coordinate lines, Remark 4): the
+// pairs of one eta_{ph+1}-line of N nodes, the facet nodes attached to it -- their
+// interface fluxes, facet-correction pairs and lift -- accumulated in registers.
+//   tetrahedra: phase 0 = eta1-lines + facets 2, 3; phase 1 = eta2-lines + facet 1;
+//               phase 2 = eta3-lines + facet 4;
+//   triangles:  phase 0 = eta1-lines + facets 2, 3; phase 1 = eta2-lines + facet 1.
+// A facet node of faces 1-3 couples only with the N volume nodes of its line, so its
+// h = B J f* - C^T 1 is complete inside the task and its lift R^T h (a 1D extrapolation
+// along the line) goes straight into the line's accumulators.  Facet-4 node (a1, b')
+// couples with all volume nodes (a1, ., .): task (a1, a2) writes h4 = B J f* of node
+// (a1, a2), then in N barrier-separated steps handles column b' = (a2 + k) mod N -- the
+// tasks sharing a1 update distinct facet nodes in every step -- and finally lifts
+// y = L2J h4 along its eta3-line.  Every thread of the block calls this (phase 2 has
+// barriers); `act` marks the threads that own a task.
+template <int D, int N>
+__device__ __forceinline__ void line_task(int ph, int t, bool act, const DevRef& R, const DevMesh& M, int64_t eg,
+                                          const double* __restrict__ Sv, const double* __restrict__ Sf, double* r,
+                                          double* h4, const double* __restrict__ vdir,
+                                          const double* __restrict__ fdir, const FluxK& K) {
   constexpr int NC = D + 2;
-  const int Nq = R.Nq, Nfn = R.Nfn, Nqf = R.Nqf, T = R.T;
+  const int Nq = R.Nq, Nfn = R.Nfn, Nqf = R.Nqf, T = R.T, Ntot = R.Ntot;
   int base, stride;
   if (D == 2) {
     base = ph == 0 ? N * t : t;
@@ -611,9 +671,9 @@ __device__ __forceinline__ void line_task(int ph, int t, const DevRef& R, const 
   for (int a = 0; a < N; ++a)
 #pragma unroll
     for (int c = 0; c < NC; ++c) acc[a][c] = 0.0;
-  constexpr int Lv = N * (N - 1) / 2;
-  const double* vd = vdir + (size_t)ph * Lv * D * T + t;
-  if (b0 == 0) {
+  if (act) {
+    constexpr int Lv = N * (N - 1) / 2;
+    const double* vd = vdir + (size_t)ph * Lv * D * T + t;
 #pragma unroll
     for (int a = 0, m = 0; a < N; ++a) {
 #pragma unroll
@@ -631,100 +691,97 @@ __device__ __forceinline__ void line_task(int ph, int t, const DevRef& R, const 
         }
       }
     }
-  }
-  if (ph == 0) {
+    if (ph == 0) {
 #pragma unroll
-    for (int zz = 0; zz < 2; ++zz) {
-      const int f = (1 + zz) * Nqf + t;
-      const double* fd = fdir + R.fph_off[0] + (size_t)zz * N * D * T + t;
-      const NodeState<D> Sj = load_state<D>(Sf, Nfn, f);
-      double hs[NC];
+      for (int zz = 0; zz < 2; ++zz) {
+        const int f = (1 + zz) * Nqf + t;
+        double hs[NC];
+        interface_flux<D>(M, Nq, Nfn, Ntot, eg, f, Sf, K, hs);
+        const NodeState<D> Sj = load_state<D>(Sf, Nfn, f);
+        facet_strip<D, N>(Sv, Nq, base, stride, Sj, fdir + R.fph_off[0] + (size_t)zz * N * D * T + t, T, K, acc,
+                          hs);
+        const double* l = zz == 0 ? R.l1p : R.l1m;   // lift of facets 2, 3 along the eta1-line
 #pragma unroll
-      for (int c = 0; c < NC; ++c) hs[c] = 0.0;
+        for (int a = 0; a < N; ++a) {
+          const double la = l[a];
 #pragma unroll
-      for (int a = 0; a < N; ++a) {
-        const NodeState<D> Si = load_state<D>(Sv, Nq, base + a * stride);
-        double nh[D], F[NC];
-#pragma unroll
-        for (int k = 0; k < D; ++k) nh[k] = fd[(a * D + k) * T];
-        ec_flux_fast<D>(Si, Sj, nh, K, F);
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-          acc[a][c] -= F[c];
-          hs[c] += F[c];
+          for (int c = 0; c < NC; ++c) acc[a][c] = fma(-la, hs[c], acc[a][c]);
         }
       }
+    } else if (ph == 1) {
+      const int f = t;
+      double hs[NC];
+      interface_flux<D>(M, Nq, Nfn, Ntot, eg, f, Sf, K, hs);
+      const NodeState<D> Sj = load_state<D>(Sf, Nfn, f);
+      facet_strip<D, N>(Sv, Nq, base, stride, Sj, fdir + R.fph_off[1] + t, T, K, acc, hs);
 #pragma unroll
-      for (int c = 0; c < NC; ++c) h[c * Nfn + f] -= hs[c];
-    }
-  } else if (ph == 1) {
-    const int f = t;
-    const double* fd = fdir + R.fph_off[1] + t;
-    const NodeState<D> Sj = load_state<D>(Sf, Nfn, f);
-    double hs[NC];
+      for (int a = 0; a < N; ++a) {   // lift of facet 1 along the eta2-line
+        const double la = R.l2m[a];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) hs[c] = 0.0;
-#pragma unroll
-    for (int a = 0; a < N; ++a) {
-      const NodeState<D> Si = load_state<D>(Sv, Nq, base + a * stride);
-      double nh[D], F[NC];
-#pragma unroll
-      for (int k = 0; k < D; ++k) nh[k] = fd[(a * D + k) * T];
-      ec_flux_fast<D>(Si, Sj, nh, K, F);
-#pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        acc[a][c] -= F[c];
-        hs[c] += F[c];
+        for (int c = 0; c < NC; ++c) acc[a][c] = fma(-la, hs[c], acc[a][c]);
       }
-    }
+    } else if (D == 3) {
+      double hs[NC];
+      interface_flux<D>(M, Nq, Nfn, Ntot, eg, 3 * Nqf + t, Sf, K, hs);
 #pragma unroll
-    for (int c = 0; c < NC; ++c) h[c * Nfn + f] -= hs[c];
-  } else if (D == 3) {
-    // facet 4: nodes (a1, b') with a1 = t % N, against the eta3-line (a1, a2 = t / N)
-    const double* fd = fdir + R.fph_off[3] + t;
-    const int a1 = t % N;
-    constexpr int NB = facet4_cols(N);
+      for (int c = 0; c < NC; ++c) h4[c * Nqf + t] = hs[c];
+    }
+  }
+  if (D == 3 && ph == 2) {
+    const int a1 = t % N, a2 = t / N;
+    const double* fd4 = act ? fdir + R.fph_off[3] + t : nullptr;
 #pragma unroll 1
-    for (int bp = b0; bp < b1; ++bp) {
-      const int f = 3 * Nqf + a1 + N * bp;
-      const NodeState<D> Sj = load_state<D>(Sf, Nfn, f);
-      double hs[NC];
+    for (int k = 0; k < N; ++k) {
+      if (act) {
+        const int bp = a2 + k < N ? a2 + k : a2 + k - N;
+        const int j = a1 + N * bp;
+        const NodeState<D> Sj = load_state<D>(Sf, Nfn, 3 * Nqf + j);
+        double hs[NC];
 #pragma unroll
-      for (int c = 0; c < NC; ++c) hs[c] = 0.0;
+        for (int c = 0; c < NC; ++c) hs[c] = 0.0;
+        facet_strip<D, N>(Sv, Nq, base, stride, Sj, fd4 + (size_t)bp * N * D * T, T, K, acc, hs);
 #pragma unroll
-      for (int a = 0; a < N; ++a) {
-        const NodeState<D> Si = load_state<D>(Sv, Nq, base + a * stride);
-        double nh[D], F[NC];
+        for (int c = 0; c < NC; ++c) h4[c * Nqf + j] += hs[c];
+      }
+      __syncthreads();
+    }
+    if (act) {   // lift of facet 4: y = sum_b' L2J[b'][a2] h4(a1, b'), along the eta3-line
+      double y[NC];
 #pragma unroll
-        for (int k = 0; k < D; ++k) nh[k] = fd[((bp * N + a) * D + k) * T];
-        ec_flux_fast<D>(Si, Sj, nh, K, F);
+      for (int c = 0; c < NC; ++c) y[c] = 0.0;
+#pragma unroll 1
+      for (int bp = 0; bp < N; ++bp) {
+        const double w = R.L2J[bp * N + a2];
 #pragma unroll
-        for (int c = 0; c < NC; ++c) {
-          acc[a][c] -= F[c];
-          hs[c] += F[c];
-        }
+        for (int c = 0; c < NC; ++c) y[c] = fma(w, h4[c * Nqf + a1 + N * bp], y[c]);
       }
 #pragma unroll
-      for (int c = 0; c < NC; ++c) part[(c * T + t) * NB + (bp - b0)] = hs[c];
+      for (int a = 0; a < N; ++a) {
+        const double la = R.l3m[a];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) acc[a][c] = fma(-la, y[c], acc[a][c]);
+      }
     }
   }
+  if (act) {
 #pragma unroll
-  for (int a = 0; a < N; ++a)
+    for (int a = 0; a < N; ++a)
 #pragma unroll
-    for (int c = 0; c < NC; ++c) r[c * Nq + base + a * stride] += acc[a][c];
+      for (int c = 0; c < NC; ++c) r[c * Nq + base + a * stride] += acc[a][c];
+  }
 }
 
 template <int D, int N>
 __device__ void residual_tile(const DevRef& R, const DevMesh& M, int64_t e0, int E, const Epilogue& ep) {
   extern __shared__ double sm[];
   constexpr int NC = D + 2, NF = D + 5;
-  const int n = R.n, Nq = R.Nq, Nfn = R.Nfn, Ntot = R.Ntot, Np = R.Np, T = R.T, Nqf = R.Nqf;
+  const int n = R.n, Nq = R.Nq, Nfn = R.Nfn, Ntot = R.Ntot, Np = R.Np, T = R.T;
   const ResLayout Ly = res_layout<D>(Nq, Nfn, Np, n);
   const int pe = Ly.pe;
   const double inv_gm1 = 1.0 / (M.gamma - 1.0);
   Tile tile{sm, pe, E};
 
-  // 1. load states
+  // 1. load states, zero the residual accumulators
   for (int idx = threadIdx.x; idx < E * NF * Ntot; idx += blockDim.x) {
     int e = idx / (NF * Ntot), r = idx % (NF * Ntot), f = r / Ntot, k = r % Ntot;
     double val = M.states[(e0 + e) * NF * Ntot + r];
@@ -738,117 +795,24 @@ __device__ void residual_tile(const DevRef& R, const DevMesh& M, int64_t e0, int
     sm[e * pe + Ly.oR + idx % (NC * Nq)] = 0.0;
   }
   __syncthreads();
-  // 2. interface flux h = B J f* (Eq. (interface_flux), Eq. (num_flux), Eq. (wave_speed))
-  for (int idx = threadIdx.x; idx < E * Nfn; idx += blockDim.x) {
-    int e = idx / Nfn, f = idx % Nfn;
-    const int64_t eg = e0 + e;
-    NodeState<D> L = load_state<D>(sm + e * pe + Ly.oSf, Nfn, f);
-    const int64_t e2 = M.nbr_e[eg * Nfn + f];
-    const int f2 = M.nbr_f[eg * Nfn + f];
-    NodeState<D> Rr = load_state<D>(M.states + e2 * NF * Ntot + Nq, Ntot, f2);
-    double nn[D], nh[D];
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
-      nn[k] = M.nrm[(eg * D + k) * Nfn + f];
-      nh[k] = 0.5 * nn[k];
-    }
-    double F[NC];
-    ec_flux_fast<D>(L, Rr, nh, make_fluxk(M.gamma), F);
-    if (M.lf) {
-      double vnL = 0.0, vnR = 0.0, vvL = 0.0, vvR = 0.0;
-#pragma unroll
-      for (int k = 0; k < D; ++k) {
-        vnL = fma(L.v[k], nn[k], vnL);
-        vnR = fma(Rr.v[k], nn[k], vnR);
-        vvL = fma(L.v[k], L.v[k], vvL);
-        vvR = fma(Rr.v[k], Rr.v[k], vvR);
-      }
-      double lam = fmax(fabs(vnL), fabs(vnR)) + fmax(M.cfac[eg * Nfn + f], M.cfac[e2 * Nfn + f2]);
-      double hl = 0.5 * lam;
-      F[0] -= hl * (Rr.rho - L.rho);
-#pragma unroll
-      for (int k = 0; k < D; ++k) F[1 + k] -= hl * (Rr.rho * Rr.v[k] - L.rho * L.v[k]);
-      double EL = L.p * inv_gm1 + 0.5 * L.rho * vvL, ER = Rr.p * inv_gm1 + 0.5 * Rr.rho * vvR;
-      F[D + 1] -= hl * (ER - EL);
-    }
-    const double bj = M.bj[eg * Nfn + f];
-    double* h = sm + e * pe + Ly.oH;
-#pragma unroll
-    for (int c = 0; c < NC; ++c) h[c * Nfn + f] = bj * F[c];
-  }
-  __syncthreads();
-  // 3. line-based flux differencing and facet correction
+  // 2. interface fluxes, line-based flux differencing, facet correction and lift
+  //    (Eq. (entropy_stable)), one line task per thread and phase
   {
     const FluxK K = make_fluxk(M.gamma);
-    const int tid = threadIdx.x;
-    const int el = tid / T, t = tid % T;
-    const bool active = el < E;
-    const int64_t eg = e0 + el;
-    const double* vdir = active ? M.vdir + eg * (int64_t)R.nvp * D : nullptr;
-    const double* fdir = active ? M.fdir + eg * (int64_t)R.nfp * D : nullptr;
-    for (int ph = 0; ph < D - 1; ++ph) {
-      if (active)
-        line_task<D, N>(ph, t, R, sm + el * pe + Ly.oSv, sm + el * pe + Ly.oSf, sm + el * pe + Ly.oR,
-                        sm + el * pe + Ly.oH, sm + el * pe + Ly.oPart, vdir, fdir, K);
+    const int el = threadIdx.x / T, t = threadIdx.x % T;
+    const bool act = el < E;
+    const int elc = act ? el : 0;
+    const int64_t eg = e0 + elc;
+    const double* vdir = act ? M.vdir + eg * (int64_t)R.nvp * D : nullptr;
+    const double* fdir = act ? M.fdir + eg * (int64_t)R.nfp * D : nullptr;
+    double* base = sm + elc * pe;
+#pragma unroll 1
+    for (int ph = 0; ph < D; ++ph) {
+      line_task<D, N>(ph, t, act, R, M, eg, base + Ly.oSv, base + Ly.oSf, base + Ly.oR, base + Ly.oH4, vdir, fdir,
+                      K);
       __syncthreads();
     }
-    if (D == 2) {
-      if (active)
-        line_task<D, N>(1, t, R, sm + el * pe + Ly.oSv, sm + el * pe + Ly.oSf, sm + el * pe + Ly.oR,
-                        sm + el * pe + Ly.oH, sm + el * pe + Ly.oPart, vdir, fdir, K);
-      __syncthreads();
-    } else {
-      // eta3 lines and facet 4, in passes over the facet-4 columns; after each pass the
-      // per-task partials are summed over a2 into h
-      constexpr int NB = facet4_cols(N);
-      for (int b0 = 0; b0 < N; b0 += NB) {
-        const int b1 = b0 + NB < N ? b0 + NB : N;
-        if (active)
-          line_task<D, N>(2, t, R, sm + el * pe + Ly.oSv, sm + el * pe + Ly.oSf, sm + el * pe + Ly.oR,
-                          sm + el * pe + Ly.oH, sm + el * pe + Ly.oPart, vdir, fdir, K, b0, b1);
-        __syncthreads();
-        const int nb = b1 - b0;
-        for (int idx = threadIdx.x; idx < E * NC * n * nb; idx += blockDim.x) {
-          int e = idx / (NC * n * nb), rr = idx % (NC * n * nb), c = rr / (n * nb), j = rr % (n * nb);
-          int a = j % n, bq = j / n;
-          const double* pp = sm + e * pe + Ly.oPart + c * T * NB;
-          double s = 0.0;
-          for (int b2 = 0; b2 < n; ++b2) s += pp[(a + n * b2) * NB + bq];
-          sm[e * pe + Ly.oH + c * Nfn + 3 * Nqf + a + n * (b0 + bq)] -= s;
-        }
-        __syncthreads();
-      }
-    }
   }
-  // 4. lift: r -= sum_zeta R^T h  (h = B J f* - C^T 1)
-  if (D == 3) {
-    // y[a + n*b2] = sum_b' L2J[b'][b2] h4[a + n*b']  (into scratch part region, free now)
-    for (int idx = threadIdx.x; idx < E * NC * n * n; idx += blockDim.x) {
-      int e = idx / (NC * n * n), rr = idx % (NC * n * n), c = rr / (n * n), ab = rr % (n * n);
-      int a = ab % n, b2 = ab / n;
-      const double* hh = sm + e * pe + Ly.oH + c * Nfn + 3 * Nqf;
-      double s = 0.0;
-      for (int bp = 0; bp < n; ++bp) s = fma(R.L2J[bp * n + b2], hh[a + n * bp], s);
-      sm[e * pe + Ly.oPart + rr] = s;
-    }
-    __syncthreads();
-  }
-  for (int idx = threadIdx.x; idx < E * NC * Nq; idx += blockDim.x) {
-    int e = idx / (NC * Nq), rr = idx % (NC * Nq), c = rr / Nq, v = rr % Nq;
-    const double* hh = sm + e * pe + Ly.oH + c * Nfn;
-    double s;
-    if (D == 2) {
-      int a = v % n, b = v / n;
-      s = R.l2m[b] * hh[a] + R.l1p[a] * hh[Nqf + b] + R.l1m[a] * hh[2 * Nqf + b];
-    } else {
-      int a = v % n, b = (v / n) % n, c3 = v / (n * n);
-      const double* y = sm + e * pe + Ly.oPart + c * n * n;
-      s = R.l2m[b] * hh[a + n * c3] + R.l1p[a] * hh[Nqf + b + n * c3] + R.l1m[a] * hh[2 * Nqf + b + n * c3] +
-          R.l3m[c3] * y[a + n * b];
-    }
-    sm[e * pe + Ly.oR + rr] -= s;
-  }
-  __syncthreads();
   if (ep.mode == 2) {
     // diagnostics: per element sum_i r_i (per variable), sum w.r, sum |w r|
     for (int e = threadIdx.x / 32; e < E; e += blockDim.x / 32) {
