@@ -104,8 +104,10 @@ esd_status esd_mesh_create(const esd_mesh_desc* desc, esd_mesh* out);
 esd_status esd_mesh_destroy(esd_mesh mesh);
 esd_status esd_mesh_info(esd_mesh mesh, esd_info* out);
 
-/* Synchronize the stream, then report (and clear) the device admissibility flag:
- * ESD_OK or ESD_ERR_STATE. */
+/* Synchronize the stream, then report (and clear) the device error flag: ESD_OK,
+ * ESD_ERR_TIMEOUT (a shared-memory staging copy did not complete within its bounded
+ * wait of about one second; that block skipped its work) or ESD_ERR_STATE (a
+ * non-admissible state). */
 esd_status esd_mesh_check(esd_mesh mesh, void* stream);
 
 /* Physical coordinates of the volume quadrature nodes, HOST output
@@ -220,6 +222,13 @@ esd_status esd_debug_host_setup(const esd_mesh_desc* desc, double* wj, double* b
 /* Test hook: y = log(x) (which = 0) or exp(x) (which = 1) elementwise with the library's
  * table-driven device implementations; x, y device arrays of n doubles. */
 esd_status esd_debug_math(int which, const double* x, double* y, int64_t n, void* stream);
+
+/* Test hook for the failure path of the bounded waits (not in the paper): launches one
+ * block that waits on a shared-memory barrier that nothing completes; after `seconds`
+ * (0 < seconds <= 10) the wait gives up and sets the mesh's error flag, so that the next
+ * esd_mesh_check returns ESD_ERR_TIMEOUT.  The kernels' staging copies use the same
+ * bounded wait (about one second). */
+esd_status esd_debug_staging_timeout(esd_mesh mesh, double seconds, void* stream);
 
 const char* esd_status_string(esd_status s);
 const char* esd_last_error(void);

@@ -66,6 +66,7 @@ SYMBOLS = {
     "esd_measure_fp64_peak": ([ctypes.POINTER(ctypes.c_double), ctypes.c_void_p], ctypes.c_int),
     "esd_ref_info": ([ctypes.c_int, ctypes.c_int, ctypes.POINTER(esd_info)], ctypes.c_int),
     "esd_debug_host_setup": ([ctypes.POINTER(esd_mesh_desc)] + [ctypes.c_void_p] * 8, ctypes.c_int),
+    "esd_debug_staging_timeout": ([ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p], ctypes.c_int),
     "esd_debug_math": ([ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p],
                        ctypes.c_int),
     "esd_status_string": ([ctypes.c_int], ctypes.c_char_p),
@@ -214,6 +215,12 @@ def esd_autotune(h, u, stream=None):
 def esd_launch_stage(h, stage, u=None, out=None, stream=None):
     _check(lib().esd_launch_stage(h, int(stage), _ptr(u) if u is not None else None,
                                   _ptr(out) if out is not None else None, _stream(stream)))
+
+
+def esd_debug_staging_timeout(handle, seconds=0.05, stream=None):
+    """Failure-path hook: a wait that nothing completes gives up after `seconds`; the next
+    esd_mesh_check reports ESD_ERR_TIMEOUT."""
+    _check(lib().esd_debug_staging_timeout(handle, float(seconds), _stream(stream)))
 
 
 def esd_debug_math(which, x, y, stream=None):

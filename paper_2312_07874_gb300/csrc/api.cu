@@ -248,9 +248,18 @@ esd_status esd_mesh_check(esd_mesh m, void* stream) {
   if (e != cudaSuccess) return cuda_fail(e, "flag read");
   if (flag) {
     cudaMemset(m->M.flag, 0, sizeof(int));
+    if (flag & kFlagTimeout)
+      return fail(ESD_ERR_TIMEOUT, "a shared-memory staging copy did not complete within its time limit");
     return fail(ESD_ERR_STATE, "non-admissible state (rho <= 0, p <= 0 or non-finite) at a quadrature node");
   }
   return ESD_OK;
+}
+
+esd_status esd_debug_staging_timeout(esd_mesh m, double seconds, void* stream) {
+  if (!m) return fail(ESD_ERR_ARG, "null mesh");
+  if (!(seconds > 0.0) || seconds > 10.0) return fail(ESD_ERR_ARG, "seconds must be in (0, 10]");
+  cudaError_t e = launch_staging_timeout_probe(m->M.flag, seconds, (cudaStream_t)stream);
+  return e ? cuda_fail(e, "timeout probe launch") : ESD_OK;
 }
 
 esd_status esd_mesh_volume_nodes(esd_mesh m, double* x) {

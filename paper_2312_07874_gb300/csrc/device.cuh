@@ -527,7 +527,7 @@ __device__ void project_tile(const DevRef& R, const DevMesh& M, int64_t e0, int 
       int e = idx / (NC * Np), r = idx % (NC * Np);
       w_modal[(e0 + e) * NC * Np + r] = sm[e * pe + oM + r];
     }
-    if (lbad) atomicOr(M.flag, 1);
+    if (lbad) atomicOr(M.flag, kFlagState);
     return;
   }
   // 7-8. w = V w~, facet values R w
@@ -545,26 +545,73 @@ __device__ void project_tile(const DevRef& R, const DevMesh& M, int64_t e0, int 
     store_state<D>(M.states + (e0 + e) * NF * Ntot, Ntot, k, st);
     if (k >= Nq) M.cfac[(e0 + e) * Nfn + (k - Nq)] = sqrt(M.gamma * st.p / st.rho);
   }
-  if (lbad) atomicOr(M.flag, 1);
+  if (lbad) atomicOr(M.flag, kFlagState);
+}
+
+// ---------------------------------------------------------------------------
+// Bulk copies global -> shared memory by the TMA unit (cp.async.bulk), completing on an
+// mbarrier in shared memory; waits are bounded (about a second), after which the kernel
+// reports the failure through the mesh's flag instead of spinning.
+// ---------------------------------------------------------------------------
+constexpr long long kWaitCycles = 2000000000LL;
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_inval(unsigned long long* bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+
+// dst, src 16-byte aligned, bytes a multiple of 16
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+
+// true once phase `parity` of the barrier has completed; false after `limit` clock cycles
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, long long limit) {
+  const long long t0 = clock64();
+  while (true) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > limit) return false;
+  }
 }
 
 // ---------------------------------------------------------------------------
 // Residual kernel
-// shared layout per element (doubles):
-//   states Sv[NF*Nq] | Sf[NF*Nfn]   (reused as transform scratch S1, S2, Mod afterwards)
+// dynamic shared memory: 16 bytes for the staging mbarrier, then per element (doubles,
+// an even count so that every element starts 16-byte aligned):
+//   states S[NF][Ntot] (volume nodes then facet nodes, the global layout; one bulk copy)
+//   -- reused as transform scratch S1, S2, Mod after the pair phases --
 //   r[NC*Nq] | h4[NC*n^2] (tetrahedra: facet-4 node accumulators)
 // ---------------------------------------------------------------------------
 struct ResLayout {
-  int oSv, oSf, oS1, oS2, oMod, oR, oH4, pe;
+  int oS, oS1, oS2, oMod, oR, oH4, pe;
 };
 
 template <int D>
 __host__ __device__ inline ResLayout res_layout(int Nq, int Nfn, int Np, int n) {
   constexpr int NC = D + 2, NF = D + 5;
   ResLayout L;
-  L.oSv = 0;
-  L.oSf = NF * Nq;
-  int r0 = L.oSf + NF * Nfn;
+  L.oS = 0;
+  int r0 = NF * (Nq + Nfn);
   L.oS1 = 0;
   L.oS2 = NC * Nq;
   L.oMod = 2 * NC * Nq;
@@ -573,8 +620,10 @@ __host__ __device__ inline ResLayout res_layout(int Nq, int Nfn, int Np, int n) 
   L.oR = r0;
   L.oH4 = L.oR + NC * Nq;
   L.pe = L.oH4 + (D == 3 ? NC * n * n : 0);
+  L.pe += L.pe & 1;
   return L;
 }
+constexpr int kResSmemHeader = 2;   // doubles before the first element (the mbarrier)
 
 // F = B J f* at facet node f of element eg (Eq. (interface_flux), Eq. (num_flux),
 // Eq. (wave_speed)): own trace from shared memory, the neighbour's from its stored states.
@@ -582,7 +631,7 @@ template <int D>
 __device__ __forceinline__ void interface_flux(const DevMesh& M, int Nq, int Nfn, int Ntot, int64_t eg, int f,
                                                const double* __restrict__ Sf, const FluxK& K, double* F) {
   constexpr int NF = D + 5;
-  const NodeState<D> L = load_state<D>(Sf, Nfn, f);
+  const NodeState<D> L = load_state<D>(Sf, Ntot, f);
   const int64_t e2 = M.nbr_e[eg * Nfn + f];
   const int f2 = M.nbr_f[eg * Nfn + f];
   const NodeState<D> Rr = load_state<D>(M.states + e2 * NF * Ntot + Nq, Ntot, f2);
@@ -618,12 +667,12 @@ __device__ __forceinline__ void interface_flux(const DevMesh& M, int Nq, int Nfn
 // N facet-correction pairs between facet node f (state Sj) and the line's volume nodes,
 // directions fd[(a * D + k) * T]: acc[a] -= F_a, hs -= F_a.
 template <int D, int N>
-__device__ __forceinline__ void facet_strip(const double* __restrict__ Sv, int Nq, int base, int stride,
+__device__ __forceinline__ void facet_strip(const double* __restrict__ Sv, int Ntot, int base, int stride,
                                             const NodeState<D>& Sj, const double* __restrict__ fd, int T,
                                             const FluxK& K, double (&acc)[N][D + 2], double* hs) {
 #pragma unroll
   for (int a = 0; a < N; ++a) {
-    const NodeState<D> Si = load_state<D>(Sv, Nq, base + a * stride);
+    const NodeState<D> Si = load_state<D>(Sv, Ntot, base + a * stride);
     double nh[D], F[D + 2];
 #pragma unroll
     for (int k = 0; k < D; ++k) nh[k] = fd[(a * D + k) * T];
@@ -678,8 +727,8 @@ __device__ __forceinline__ void line_task(int ph, int t, bool act, const DevRef&
     for (int a = 0, m = 0; a < N; ++a) {
 #pragma unroll
       for (int b = a + 1; b < N; ++b, ++m) {
-        const NodeState<D> Si = load_state<D>(Sv, Nq, base + a * stride);
-        const NodeState<D> Sj = load_state<D>(Sv, Nq, base + b * stride);
+        const NodeState<D> Si = load_state<D>(Sv, Ntot, base + a * stride);
+        const NodeState<D> Sj = load_state<D>(Sv, Ntot, base + b * stride);
         double nh[D], F[NC];
 #pragma unroll
         for (int k = 0; k < D; ++k) nh[k] = vd[(m * D + k) * T];
@@ -697,8 +746,8 @@ __device__ __forceinline__ void line_task(int ph, int t, bool act, const DevRef&
         const int f = (1 + zz) * Nqf + t;
         double hs[NC];
         interface_flux<D>(M, Nq, Nfn, Ntot, eg, f, Sf, K, hs);
-        const NodeState<D> Sj = load_state<D>(Sf, Nfn, f);
-        facet_strip<D, N>(Sv, Nq, base, stride, Sj, fdir + R.fph_off[0] + (size_t)zz * N * D * T + t, T, K, acc,
+        const NodeState<D> Sj = load_state<D>(Sf, Ntot, f);
+        facet_strip<D, N>(Sv, Ntot, base, stride, Sj, fdir + R.fph_off[0] + (size_t)zz * N * D * T + t, T, K, acc,
                           hs);
         const double* l = zz == 0 ? R.l1p : R.l1m;   // lift of facets 2, 3 along the eta1-line
 #pragma unroll
@@ -712,8 +761,8 @@ __device__ __forceinline__ void line_task(int ph, int t, bool act, const DevRef&
       const int f = t;
       double hs[NC];
       interface_flux<D>(M, Nq, Nfn, Ntot, eg, f, Sf, K, hs);
-      const NodeState<D> Sj = load_state<D>(Sf, Nfn, f);
-      facet_strip<D, N>(Sv, Nq, base, stride, Sj, fdir + R.fph_off[1] + t, T, K, acc, hs);
+      const NodeState<D> Sj = load_state<D>(Sf, Ntot, f);
+      facet_strip<D, N>(Sv, Ntot, base, stride, Sj, fdir + R.fph_off[1] + t, T, K, acc, hs);
 #pragma unroll
       for (int a = 0; a < N; ++a) {   // lift of facet 1 along the eta2-line
         const double la = R.l2m[a];
@@ -735,11 +784,11 @@ __device__ __forceinline__ void line_task(int ph, int t, bool act, const DevRef&
       if (act) {
         const int bp = a2 + k < N ? a2 + k : a2 + k - N;
         const int j = a1 + N * bp;
-        const NodeState<D> Sj = load_state<D>(Sf, Nfn, 3 * Nqf + j);
+        const NodeState<D> Sj = load_state<D>(Sf, Ntot, 3 * Nqf + j);
         double hs[NC];
 #pragma unroll
         for (int c = 0; c < NC; ++c) hs[c] = 0.0;
-        facet_strip<D, N>(Sv, Nq, base, stride, Sj, fd4 + (size_t)bp * N * D * T, T, K, acc, hs);
+        facet_strip<D, N>(Sv, Ntot, base, stride, Sj, fd4 + (size_t)bp * N * D * T, T, K, acc, hs);
 #pragma unroll
         for (int c = 0; c < NC; ++c) h4[c * Nqf + j] += hs[c];
       }
@@ -773,7 +822,9 @@ __device__ __forceinline__ void line_task(int ph, int t, bool act, const DevRef&
 
 template <int D, int N>
 __device__ void residual_tile(const DevRef& R, const DevMesh& M, int64_t e0, int E, const Epilogue& ep) {
-  extern __shared__ double sm[];
+  extern __shared__ double sm_raw[];
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(sm_raw);
+  double* const sm = sm_raw + kResSmemHeader;
   constexpr int NC = D + 2, NF = D + 5;
   const int n = R.n, Nq = R.Nq, Nfn = R.Nfn, Ntot = R.Ntot, Np = R.Np, T = R.T;
   const ResLayout Ly = res_layout<D>(Nq, Nfn, Np, n);
@@ -781,20 +832,42 @@ __device__ void residual_tile(const DevRef& R, const DevMesh& M, int64_t e0, int
   const double inv_gm1 = 1.0 / (M.gamma - 1.0);
   Tile tile{sm, pe, E};
 
-  // 1. load states, zero the residual accumulators
-  for (int idx = threadIdx.x; idx < E * NF * Ntot; idx += blockDim.x) {
-    int e = idx / (NF * Ntot), r = idx % (NF * Ntot), f = r / Ntot, k = r % Ntot;
-    double val = M.states[(e0 + e) * NF * Ntot + r];
-    if (k < Nq)
-      sm[e * pe + Ly.oSv + f * Nq + k] = val;
-    else
-      sm[e * pe + Ly.oSf + f * Nfn + (k - Nq)] = val;
+  // 1. stage the elements' states with one bulk copy each (TMA), zero the residual
+  //    accumulators meanwhile
+  // (NF*Ntot*8 bytes per element is a multiple of 16; elements start 16-byte aligned)
+  const unsigned bytes = (unsigned)(NF * Ntot * sizeof(double));
+  const bool tma = ((smem_addr(sm) & 15u) | (unsigned)(reinterpret_cast<uintptr_t>(M.states) & 15)) == 0;
+  if (tma) {
+    if (threadIdx.x == 0) mbar_init(bar);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // earlier shared writes before the copies
+      mbar_arrive_expect_tx(bar, bytes * (unsigned)E);
+      for (int e = 0; e < E; ++e) bulk_copy_g2s(sm + e * pe + Ly.oS, M.states + (e0 + e) * NF * Ntot, bytes, bar);
+    }
+  } else {
+    for (int idx = threadIdx.x; idx < E * NF * Ntot; idx += blockDim.x) {
+      const int e = idx / (NF * Ntot);
+      sm[e * pe + Ly.oS + idx % (NF * Ntot)] = M.states[e0 * NF * Ntot + idx];
+    }
   }
   for (int idx = threadIdx.x; idx < E * NC * Nq; idx += blockDim.x) {
     int e = idx / (NC * Nq);
     sm[e * pe + Ly.oR + idx % (NC * Nq)] = 0.0;
   }
-  __syncthreads();
+  if (tma) {
+    const bool staged = mbar_wait(bar, 0, kWaitCycles);
+    if (!__syncthreads_and(staged)) {
+      if (threadIdx.x == 0) {
+        atomicOr(M.flag, kFlagTimeout);
+        mbar_wait(bar, 0, kWaitCycles);   // let copies still in flight land before the block exits
+      }
+      return;
+    }
+    if (threadIdx.x == 0) mbar_inval(bar);
+  } else {
+    __syncthreads();
+  }
   // 2. interface fluxes, line-based flux differencing, facet correction and lift
   //    (Eq. (entropy_stable)), one line task per thread and phase
   {
@@ -808,8 +881,8 @@ __device__ void residual_tile(const DevRef& R, const DevMesh& M, int64_t e0, int
     double* base = sm + elc * pe;
 #pragma unroll 1
     for (int ph = 0; ph < D; ++ph) {
-      line_task<D, N>(ph, t, act, R, M, eg, base + Ly.oSv, base + Ly.oSf, base + Ly.oR, base + Ly.oH4, vdir, fdir,
-                      K);
+      line_task<D, N>(ph, t, act, R, M, eg, base + Ly.oS, base + Ly.oS + Nq, base + Ly.oR, base + Ly.oH4, vdir,
+                      fdir, K);
       __syncthreads();
     }
   }
@@ -821,7 +894,7 @@ __device__ void residual_tile(const DevRef& R, const DevMesh& M, int64_t e0, int
 #pragma unroll
       for (int c = 0; c < NC + 2; ++c) acc[c] = 0.0;
       for (int v = lane; v < Nq; v += 32) {
-        NodeState<D> s = load_state<D>(sm + e * pe + Ly.oSv, Nq, v);
+        NodeState<D> s = load_state<D>(sm + e * pe + Ly.oS, Ntot, v);
         double vv = 0.0;
 #pragma unroll
         for (int k = 0; k < D; ++k) vv += s.v[k] * s.v[k];

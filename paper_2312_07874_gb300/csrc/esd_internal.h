@@ -83,6 +83,10 @@ struct DevRef {
   const double* mtab;   // kMathTabSize doubles
 };
 
+// bits of DevMesh::flag (read and cleared by esd_mesh_check)
+constexpr int kFlagState = 1;     // a non-admissible state (rho <= 0, p <= 0, non-finite)
+constexpr int kFlagTimeout = 2;   // a shared-memory staging copy did not complete in time
+
 struct DevMesh {
   int64_t E;
   const double *vdir, *fdir, *wj, *wdj, *bj, *nrm;
@@ -164,6 +168,7 @@ cudaError_t set_residual_smem_d3_hi(int lim);
 cudaError_t launch_reduce_diag(const double* part, int64_t E, int ncol, double* out, cudaStream_t s);
 cudaError_t launch_copy(const double* src, double* dst, int64_t n, cudaStream_t s);
 cudaError_t measure_fp64(double* flops, cudaStream_t s);
+cudaError_t launch_staging_timeout_probe(int* flag, double seconds, cudaStream_t s);
 cudaError_t launch_math_probe(int which, const double* mtab, const double* x, double* y, int64_t n, cudaStream_t s);
 cudaError_t set_smem_limits(const LaunchCfg& L, int dim);
 

@@ -394,6 +394,17 @@ __global__ void math_probe_kernel(int which, const double* __restrict__ mt, cons
     y[i] = which == 0 ? log_tab(x[i], mt) : exp_tab(x[i], mt);
 }
 
+// Failure-path check of the bounded staging wait: an mbarrier expecting a transaction
+// that no copy will complete; the wait gives up after `limit` cycles and sets the flag.
+__global__ void staging_timeout_probe_kernel(int* flag, long long limit) {
+  __shared__ unsigned long long bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar);
+    mbar_arrive_expect_tx(&bar, 16);
+    if (!mbar_wait(&bar, 0, limit)) atomicOr(flag, kFlagTimeout);
+  }
+}
+
 __global__ void fp64_fma_kernel(double* out, int iters) {
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   double a[8];
@@ -419,7 +430,7 @@ size_t smem_project(const RefTables& r, int e) {
 
 size_t smem_residual(const RefTables& r, int e) {
   ResLayout L = r.dim == 2 ? res_layout<2>(r.Nq, r.Nfn, r.Np, r.n) : res_layout<3>(r.Nq, r.Nfn, r.Np, r.n);
-  return (size_t)e * L.pe * sizeof(double);
+  return ((size_t)e * L.pe + kResSmemHeader) * sizeof(double);
 }
 
 static constexpr size_t kSmemBudget = 227 * 1024;   // opt-in maximum per CTA
@@ -590,6 +601,17 @@ cudaError_t launch_copy(const double* src, double* dst, int64_t n, cudaStream_t 
 
 cudaError_t launch_math_probe(int which, const double* mtab, const double* x, double* y, int64_t n, cudaStream_t s) {
   math_probe_kernel<<<152 * 4, 256, 0, s>>>(which, mtab, x, y, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_staging_timeout_probe(int* flag, double seconds, cudaStream_t s) {
+  int dev = 0, khz = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e) return e;
+  e = cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);
+  if (e) return e;
+  const long long limit = (long long)(seconds * 1e3 * (khz > 0 ? khz : 2000000));
+  staging_timeout_probe_kernel<<<1, 32, 0, s>>>(flag, limit);
   return cudaGetLastError();
 }
 
