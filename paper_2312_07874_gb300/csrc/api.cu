@@ -164,6 +164,7 @@ esd_status esd_mesh_create(const esd_mesh_desc* d, esd_mesh* out) {
   R.dense_minv = r.dense_minv;
   R.mtab = dtab + o_mt;
   R.off1 = itab + r.i_off1; R.s12a1 = itab + r.i_s12a1; R.moff = itab + r.i_moff; R.mode = itab + r.i_mode;
+  R.s12len = itab + r.i_s12len;
   // per-element data
   DevMesh& M = m->M;
   M.E = m->E;

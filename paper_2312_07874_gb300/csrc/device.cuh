@@ -85,6 +85,18 @@ __device__ __forceinline__ void ec_flux(const NodeState<D>& L, const NodeState<D
 //   relative for u < 1e-4); 1/((gamma-1) beta_ln) = K(u)/(a+b) with K = 2F/(gamma-1).
 // * Pair directions are stored halved (n/2), which absorbs the arithmetic means.
 // ---------------------------------------------------------------------------
+// 1/sqrt(a), a > 0 normal: hardware estimate, then two Newton steps y <- y (3 - a y^2)/2
+__device__ __forceinline__ double rsqrt_nr(double a) {
+  double y;
+  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(a));
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const double h = 0.5 * a * y;
+    y = fma(y, fma(-h, y, 0.5), y);
+  }
+  return y;
+}
+
 template <int NR>
 __device__ __forceinline__ double rcp_nr(double a) {
   double x;
@@ -207,13 +219,18 @@ struct Tile {
 
 // out = V in  (modal -> nodal), using scratch s1 (and s2 for tetrahedra).  All buffers
 // distinct, except that for tetrahedra `out` may equal s1.
+// The stages whose sums run over a triangular index range are enumerated with the
+// (element, variable) index fastest and, for the alpha3 stage, the (alpha1, alpha2)
+// pairs by decreasing sum length: neighbouring threads then run loops of equal length
+// (an FP64 instruction costs the same whatever the number of active lanes).
 template <int D>
 __device__ void apply_V(const DevRef& R, const Tile& t, int in, int s1, int s2, int out, int nc) {
   const int n = R.n, p = R.p;
+  const int EV = t.E * nc;
   if (D == 2) {
     int rows = (p + 1) * n, tot = t.E * nc * rows;
     for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
-      int row = idx % rows, ev = idx / rows, var = ev % nc, e = ev / nc;
+      int row = idx / EV, ev = idx % EV, var = ev % nc, e = ev / nc;
       int a1 = row / n, c2 = row % n;
       const double* x = t.base + e * t.pe + in + var * R.Np;
       int m0 = R.off1[a1];
@@ -237,8 +254,8 @@ __device__ void apply_V(const DevRef& R, const Tile& t, int in, int s1, int s2, 
     // stage 1: contract alpha3 -> [s12][c3]   (into s1)
     int rows = R.S12 * n, tot = t.E * nc * rows;
     for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
-      int row = idx % rows, ev = idx / rows, var = ev % nc, e = ev / nc;
-      int s = row / n, c3 = row % n;
+      const int rank = idx / EV, ev = idx % EV, var = ev % nc, e = ev / nc;
+      const int s = R.s12len[rank / n], c3 = rank % n, row = s * n + c3;
       int a1 = R.s12a1[s], a2 = s - R.off1[a1], m0 = R.moff[s];
       const double* x = t.base + e * t.pe + in + var * R.Np;
       double acc = 0.0;
@@ -250,7 +267,7 @@ __device__ void apply_V(const DevRef& R, const Tile& t, int in, int s1, int s2, 
     rows = (p + 1) * n * n;
     tot = t.E * nc * rows;
     for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
-      int row = idx % rows, ev = idx / rows, var = ev % nc, e = ev / nc;
+      int row = idx / EV, ev = idx % EV, var = ev % nc, e = ev / nc;
       int c3 = row % n, c2 = (row / n) % n, a1 = row / (n * n);
       const double* y = t.base + e * t.pe + s1 + var * R.Nq;
       int s0 = R.off1[a1];
@@ -534,6 +551,7 @@ __device__ void project_tile(const DevRef& R, const DevMesh& M, int64_t e0, int 
   apply_V<D>(R, t, oM, oB, oC, oA, NC);
   apply_R<D>(R, t, oA, oB, oF, NC);
   // 9. entropy-projected conservative states at volume and facet nodes
+  const double sqrt_gamma = sqrt(M.gamma);
   for (int idx = threadIdx.x; idx < E * Ntot; idx += blockDim.x) {
     int e = idx / Ntot, k = idx % Ntot;
     double ww[NC];
@@ -543,7 +561,7 @@ __device__ void project_tile(const DevRef& R, const DevMesh& M, int64_t e0, int 
     for (int c = 0; c < NC; ++c) ww[c] = src[c * str];
     NodeState<D> st = state_from_entropy<D>(ww, M.gamma, &lbad, R.mtab);
     store_state<D>(M.states + (e0 + e) * NF * Ntot, Ntot, k, st);
-    if (k >= Nq) M.cfac[(e0 + e) * Nfn + (k - Nq)] = sqrt(M.gamma * st.p / st.rho);
+    if (k >= Nq) M.cfac[(e0 + e) * Nfn + (k - Nq)] = sqrt_gamma * rsqrt_nr(st.beta);   // sqrt(gamma p / rho)
   }
   if (lbad) atomicOr(M.flag, kFlagState);
 }

@@ -38,7 +38,8 @@ struct RefTables {
   std::vector<double> l1m, l1p, l2m, l3m, L2J;
   std::vector<double> psi1, psi2, psi3;
   std::vector<int> ints;              // off1[p+1] | s12_a1[S12] | moff[S12] | mode_s12[Np] (tri: mode_a1[Np])
-  int i_off1 = 0, i_s12a1 = 0, i_moff = 0, i_mode = 0;
+                                      // | s12 by decreasing alpha3 length [S12] (tets)
+  int i_off1 = 0, i_s12a1 = 0, i_moff = 0, i_mode = 0, i_s12len = 0;
   std::vector<double> wvol;           // [Nq]
   std::vector<double> wfac;           // [Nfn]
   std::vector<double> xi_vol, xi_fac; // [Nq*dim], [Nfn*dim]
@@ -76,7 +77,7 @@ struct DevRef {
   int dim, p, n, Nq, Np, Nf, Nqf, Nfn, Ntot, T, Lv, S12, nvp, nfp;
   int fph_off[4], fph_len[4];
   const double *psi1, *psi2, *psi3;
-  const int *off1, *s12a1, *moff, *mode;
+  const int *off1, *s12a1, *moff, *mode, *s12len;
   const double *l1m, *l1p, *l2m, *l3m, *L2J;
   const double* wvol;
   int dense_minv;

@@ -317,6 +317,18 @@ esd_status build_ref(int dim, int p, RefTables* R, std::string* err) {
   r.ints.insert(r.ints.end(), moff.begin(), moff.end());
   r.i_mode = (int)r.ints.size();
   r.ints.insert(r.ints.end(), mode.begin(), mode.end());
+  // (alpha1, alpha2) pairs ordered by decreasing length p + 1 - alpha1 - alpha2 of their
+  // alpha3 sums, so that neighbouring threads of the first V stage run equal loops
+  r.i_s12len = (int)r.ints.size();
+  if (dim == 3) {
+    std::vector<int> ord(r.S12);
+    for (int s = 0; s < r.S12; ++s) ord[s] = s;
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) {
+      const int la = p - s12a1[a] - (a - off1[s12a1[a]]), lb = p - s12a1[b] - (b - off1[s12a1[b]]);
+      return la > lb;
+    });
+    r.ints.insert(r.ints.end(), ord.begin(), ord.end());
+  }
   r.ints.push_back(0);
   // volume nodes, weights (Eq. (tri_quadrature), Eq. (tet_quadrature)), chain-rule factors
   r.wvol.assign(r.Nq, 0.0);
