@@ -192,6 +192,12 @@ esd_status esd_batch_rk_step(esd_batch batch, double* const* u, const double* dt
  * variable ESD_AUTOTUNE_VERBOSE=1 every candidate's time is printed to stderr. */
 esd_status esd_autotune(esd_mesh mesh, const double* u, void* stream);
 
+/* The same for a subset of the kernels: `kernels` is a bitwise or of the ESD_TUNE_* bits
+ * (ESD_ERR_ARG for other bits); esd_autotune == ESD_TUNE_ALL.  Shapes of the kernels not
+ * selected are kept. */
+enum { ESD_TUNE_PROJECT = 1, ESD_TUNE_RESIDUAL = 2, ESD_TUNE_ADJOINT = 4, ESD_TUNE_ALL = 7 };
+esd_status esd_autotune_kernels(esd_mesh mesh, const double* u, int kernels, void* stream);
+
 /* Measurement hook: launch one kernel of the esd_rhs pipeline alone, so that it can be
  * timed with events on `stream`.  stage 0: the projection kernel on u (entropy projection
  * and entropy-projected states at all nodes, written to the handle's workspace; `out`

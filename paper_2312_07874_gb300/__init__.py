@@ -61,6 +61,7 @@ SYMBOLS = {
     "esd_batch_rk_step": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_double),
                            ctypes.c_void_p], ctypes.c_int),
     "esd_autotune": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "esd_autotune_kernels": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p], ctypes.c_int),
     "esd_launch_stage": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
                          ctypes.c_int),
     "esd_measure_fp64_peak": ([ctypes.POINTER(ctypes.c_double), ctypes.c_void_p], ctypes.c_int),
@@ -208,8 +209,15 @@ def esd_diagnostics(h, u, out, stream=None):
     _check(lib().esd_diagnostics(h, _ptr(u), _ptr(out), _stream(stream)))
 
 
+ESD_TUNE_PROJECT, ESD_TUNE_RESIDUAL, ESD_TUNE_ADJOINT, ESD_TUNE_ALL = 1, 2, 4, 7
+
+
 def esd_autotune(h, u, stream=None):
     _check(lib().esd_autotune(h, _ptr(u), _stream(stream)))
+
+
+def esd_autotune_kernels(h, u, kernels, stream=None):
+    _check(lib().esd_autotune_kernels(h, _ptr(u), int(kernels), _stream(stream)))
 
 
 def esd_launch_stage(h, stage, u=None, out=None, stream=None):
@@ -316,7 +324,9 @@ class Mesh:
     def check(self):
         esd_mesh_check(self.handle)
 
-    def autotune(self, u):
-        esd_autotune(self.handle, u)
+    def autotune(self, u, kernels=ESD_TUNE_ALL):
+        """Time launch shapes on this mesh and state u and keep the fastest (esd_autotune);
+        `kernels` selects the projection / residual / adjoint kernels (ESD_TUNE_* bits)."""
+        esd_autotune_kernels(self.handle, u, kernels)
         self.info = esd_mesh_info(self.handle)
         return self.info

@@ -728,7 +728,12 @@ static float time_launches(const std::function<cudaError_t()>& f, cudaStream_t s
 }
 
 esd_status esd_autotune(esd_mesh m, const double* u, void* stream) {
+  return esd_autotune_kernels(m, u, ESD_TUNE_ALL, stream);
+}
+
+esd_status esd_autotune_kernels(esd_mesh m, const double* u, int kernels, void* stream) {
   if (!m) return fail(ESD_ERR_ARG, "null mesh");
+  if (kernels & ~ESD_TUNE_ALL) return fail(ESD_ERR_ARG, "unknown kernel bits");
   esd_status st;
   if ((st = check_dev(u, "u"))) return st;
   cudaStream_t s = (cudaStream_t)stream;
@@ -738,7 +743,7 @@ esd_status esd_autotune(esd_mesh m, const double* u, void* stream) {
   const char* ev = std::getenv("ESD_AUTOTUNE_VERBOSE");   // print every candidate's time
   const bool verbose = ev && ev[0] == '1';
   // projection: elements per CTA x threads
-  {
+  if (kernels & ESD_TUNE_PROJECT) {
     float tbest = 1e30f;
     const int emax = std::max(1, (int)(budget / smem_project(r, 1)));
     for (int e = emax; e >= 1; e = e > 1 ? e / 2 : 0) {
@@ -760,7 +765,7 @@ esd_status esd_autotune(esd_mesh m, const double* u, void* stream) {
     }
   }
   // residual: elements per CTA (threads follow: E * line tasks rounded to warps)
-  {
+  if (kernels & ESD_TUNE_RESIDUAL) {
     cudaError_t e0 = launch_project(m->R, m->M, best, u, nullptr, s);
     if (e0) return cuda_fail(e0, "autotune projection");
     Epilogue ep{};
@@ -784,7 +789,7 @@ esd_status esd_autotune(esd_mesh m, const double* u, void* stream) {
     }
   }
   // residual adjoint (esd_rhs_vjp): elements per CTA
-  {
+  if (kernels & ESD_TUNE_ADJOINT) {
     float tbest = 1e30f;
     const int emax = std::min(std::max(1, (int)(budget / smem_residual_adj(r, 1))), std::max(1, 1024 / r.T));
     for (int e = 1; e <= emax; ++e) {
