@@ -217,6 +217,41 @@ struct Tile {
   int E;          // elements in this tile
 };
 
+// A contraction output: dst = sum_{j < len} c[j cs] x[j xs].
+struct Dot {
+  const double* c;
+  int cs;
+  const double* x;
+  int xs;
+  double* dst;
+};
+
+// Evaluates the tot outputs described by setup(idx) (all of length len), four per thread at
+// a time: each output is a chain of dependent FMAs (a 64-cycle latency apiece on this
+// FP64 pipe), and four independent chains interleave.  The summation order of every output
+// is the plain j = 0, 1, ... order.
+template <class F>
+__device__ __forceinline__ void contract4(int tot, int len, F&& setup) {
+  const int bd = blockDim.x;
+  for (int i0 = threadIdx.x; i0 < tot; i0 += 4 * bd) {
+    Dot d[4];
+    bool ok[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int idx = i0 + u * bd;
+      ok[u] = idx < tot;
+      d[u] = setup(ok[u] ? idx : i0);
+    }
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int j = 0; j < len; ++j)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc[u] = fma(d[u].c[j * d[u].cs], d[u].x[j * d[u].xs], acc[u]);
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (ok[u]) *d[u].dst = acc[u];
+  }
+}
+
 // out = V in  (modal -> nodal), using scratch s1 (and s2 for tetrahedra).  All buffers
 // distinct, except that for tetrahedra `out` may equal s1.
 // The stages whose sums run over a triangular index range are enumerated with the
@@ -241,14 +276,11 @@ __device__ void apply_V(const DevRef& R, const Tile& t, int in, int s1, int s2, 
     __syncthreads();
     rows = R.Nq;
     tot = t.E * nc * rows;
-    for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
-      int v = idx % rows, ev = idx / rows, var = ev % nc, e = ev / nc;
-      int c1 = v % n, c2 = v / n;
-      const double* y = t.base + e * t.pe + s1 + var * R.Nq;
-      double acc = 0.0;
-      for (int a1 = 0; a1 <= p; ++a1) acc = fma(R.psi1[a1 * n + c1], y[a1 * n + c2], acc);
-      t.base[e * t.pe + out + var * R.Nq + v] = acc;
-    }
+    contract4(tot, p + 1, [&](int idx) {
+      const int v = idx % rows, ev = idx / rows, var = ev % nc, e = ev / nc;
+      const int c1 = v % n, c2 = v / n;
+      return Dot{R.psi1 + c1, n, t.base + e * t.pe + s1 + var * R.Nq + c2, n, t.base + e * t.pe + out + var * R.Nq + v};
+    });
     __syncthreads();
   } else {
     // stage 1: contract alpha3 -> [s12][c3]   (into s1)
@@ -279,14 +311,12 @@ __device__ void apply_V(const DevRef& R, const Tile& t, int in, int s1, int s2, 
     // stage 3: contract alpha1 -> nodal
     rows = R.Nq;
     tot = t.E * nc * rows;
-    for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
-      int v = idx % rows, ev = idx / rows, var = ev % nc, e = ev / nc;
-      int c1 = v % n, c2 = (v / n) % n, c3 = v / (n * n);
-      const double* y = t.base + e * t.pe + s2 + var * R.Nq;
-      double acc = 0.0;
-      for (int a1 = 0; a1 <= p; ++a1) acc = fma(R.psi1[a1 * n + c1], y[(a1 * n + c2) * n + c3], acc);
-      t.base[e * t.pe + out + var * R.Nq + v] = acc;
-    }
+    contract4(tot, p + 1, [&](int idx) {
+      const int v = idx % rows, ev = idx / rows, var = ev % nc, e = ev / nc;
+      const int c1 = v % n, c2 = (v / n) % n, c3 = v / (n * n);
+      return Dot{R.psi1 + c1, n, t.base + e * t.pe + s2 + var * R.Nq + c2 * n + c3, n * n,
+                 t.base + e * t.pe + out + var * R.Nq + v};
+    });
     __syncthreads();
   }
 }
@@ -297,58 +327,48 @@ __device__ void apply_VT(const DevRef& R, const Tile& t, int in, int s1, int s2,
   const int n = R.n, p = R.p;
   if (D == 2) {
     int rows = (p + 1) * n, tot = t.E * nc * rows;
-    for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
-      int row = idx % rows, ev = idx / rows, var = ev % nc, e = ev / nc;
-      int a1 = row / n, c2 = row % n;
-      const double* x = t.base + e * t.pe + in + var * R.Nq;
-      double acc = 0.0;
-      for (int c1 = 0; c1 < n; ++c1) acc = fma(R.psi1[a1 * n + c1], x[c1 + n * c2], acc);
-      t.base[e * t.pe + s1 + var * R.Nq + row] = acc;
-    }
+    contract4(tot, n, [&](int idx) {
+      const int row = idx % rows, ev = idx / rows, var = ev % nc, e = ev / nc;
+      const int a1 = row / n, c2 = row % n;
+      return Dot{R.psi1 + a1 * n, 1, t.base + e * t.pe + in + var * R.Nq + n * c2, 1,
+                 t.base + e * t.pe + s1 + var * R.Nq + row};
+    });
     __syncthreads();
     rows = R.Np;
     tot = t.E * nc * rows;
-    for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
-      int m = idx % rows, ev = idx / rows, var = ev % nc, e = ev / nc;
-      int a1 = R.mode[m];
-      const double* y = t.base + e * t.pe + s1 + var * R.Nq;
-      double acc = 0.0;
-      for (int c2 = 0; c2 < n; ++c2) acc = fma(R.psi2[m * n + c2], y[a1 * n + c2], acc);
-      t.base[e * t.pe + out + var * R.Np + m] = acc;
-    }
+    contract4(tot, n, [&](int idx) {
+      const int m = idx % rows, ev = idx / rows, var = ev % nc, e = ev / nc;
+      const int a1 = R.mode[m];
+      return Dot{R.psi2 + m * n, 1, t.base + e * t.pe + s1 + var * R.Nq + a1 * n, 1,
+                 t.base + e * t.pe + out + var * R.Np + m};
+    });
     __syncthreads();
   } else {
     int rows = (p + 1) * n * n, tot = t.E * nc * rows;
-    for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
-      int row = idx % rows, ev = idx / rows, var = ev % nc, e = ev / nc;
-      int c3 = row % n, c2 = (row / n) % n, a1 = row / (n * n);
-      const double* x = t.base + e * t.pe + in + var * R.Nq;
-      double acc = 0.0;
-      for (int c1 = 0; c1 < n; ++c1) acc = fma(R.psi1[a1 * n + c1], x[c1 + n * (c2 + n * c3)], acc);
-      t.base[e * t.pe + s1 + var * R.Nq + row] = acc;
-    }
+    contract4(tot, n, [&](int idx) {
+      const int row = idx % rows, ev = idx / rows, var = ev % nc, e = ev / nc;
+      const int c3 = row % n, c2 = (row / n) % n, a1 = row / (n * n);
+      return Dot{R.psi1 + a1 * n, 1, t.base + e * t.pe + in + var * R.Nq + n * (c2 + n * c3), 1,
+                 t.base + e * t.pe + s1 + var * R.Nq + row};
+    });
     __syncthreads();
     rows = R.S12 * n;
     tot = t.E * nc * rows;
-    for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
-      int row = idx % rows, ev = idx / rows, var = ev % nc, e = ev / nc;
-      int s = row / n, c3 = row % n, a1 = R.s12a1[s];
-      const double* y = t.base + e * t.pe + s1 + var * R.Nq;
-      double acc = 0.0;
-      for (int c2 = 0; c2 < n; ++c2) acc = fma(R.psi2[s * n + c2], y[(a1 * n + c2) * n + c3], acc);
-      t.base[e * t.pe + s2 + var * R.Nq + row] = acc;
-    }
+    contract4(tot, n, [&](int idx) {
+      const int row = idx % rows, ev = idx / rows, var = ev % nc, e = ev / nc;
+      const int s = row / n, c3 = row % n, a1 = R.s12a1[s];
+      return Dot{R.psi2 + s * n, 1, t.base + e * t.pe + s1 + var * R.Nq + a1 * n * n + c3, n,
+                 t.base + e * t.pe + s2 + var * R.Nq + row};
+    });
     __syncthreads();
     rows = R.Np;
     tot = t.E * nc * rows;
-    for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
-      int m = idx % rows, ev = idx / rows, var = ev % nc, e = ev / nc;
-      int s = R.mode[m];
-      const double* y = t.base + e * t.pe + s2 + var * R.Nq;
-      double acc = 0.0;
-      for (int c3 = 0; c3 < n; ++c3) acc = fma(R.psi3[m * n + c3], y[s * n + c3], acc);
-      t.base[e * t.pe + out + var * R.Np + m] = acc;
-    }
+    contract4(tot, n, [&](int idx) {
+      const int m = idx % rows, ev = idx / rows, var = ev % nc, e = ev / nc;
+      const int s = R.mode[m];
+      return Dot{R.psi3 + m * n, 1, t.base + e * t.pe + s2 + var * R.Nq + s * n, 1,
+                 t.base + e * t.pe + out + var * R.Np + m};
+    });
     __syncthreads();
   }
 }
@@ -358,43 +378,28 @@ template <int D>
 __device__ void apply_R(const DevRef& R, const Tile& t, int in, int y, int out, int nc) {
   const int n = R.n;
   if (D == 3) {
-    int rows = n * n, tot = t.E * nc * rows;
-    for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {  // face 4: extrapolate eta3 -> -1
-      int row = idx % rows, ev = idx / rows, var = ev % nc, e = ev / nc;
-      const double* w = t.base + e * t.pe + in + var * R.Nq;
-      double acc = 0.0;
-      for (int c3 = 0; c3 < n; ++c3) acc = fma(R.l3m[c3], w[row + n * n * c3], acc);
-      t.base[e * t.pe + y + var * R.Nq + row] = acc;
-    }
+    const int rows = n * n, tot = t.E * nc * rows;
+    contract4(tot, n, [&](int idx) {   // face 4: extrapolate eta3 -> -1
+      const int row = idx % rows, ev = idx / rows, var = ev % nc, e = ev / nc;
+      return Dot{R.l3m, 1, t.base + e * t.pe + in + var * R.Nq + row, n * n, t.base + e * t.pe + y + var * R.Nq + row};
+    });
     __syncthreads();
   }
-  int tot = t.E * nc * R.Nfn;
-  for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
-    int f = idx % R.Nfn, ev = idx / R.Nfn, var = ev % nc, e = ev / nc;
-    int z = f / R.Nqf, j = f % R.Nqf;
+  const int tot = t.E * nc * R.Nfn;
+  contract4(tot, n, [&](int idx) {
+    const int f = idx % R.Nfn, ev = idx / R.Nfn, var = ev % nc, e = ev / nc;
+    const int z = f / R.Nqf, j = f % R.Nqf;
     const double* w = t.base + e * t.pe + in + var * R.Nq;
-    double acc = 0.0;
+    double* dst = t.base + e * t.pe + out + var * R.Nfn + f;
     if (D == 2) {
-      if (z == 0)
-        for (int b = 0; b < n; ++b) acc = fma(R.l2m[b], w[j + n * b], acc);
-      else {
-        const double* l = z == 1 ? R.l1p : R.l1m;
-        for (int a = 0; a < n; ++a) acc = fma(l[a], w[a + n * j], acc);
-      }
-    } else {
-      int a = j % n, b = j / n;
-      if (z == 0) {
-        for (int c2 = 0; c2 < n; ++c2) acc = fma(R.l2m[c2], w[a + n * (c2 + n * b)], acc);
-      } else if (z < 3) {
-        const double* l = z == 1 ? R.l1p : R.l1m;
-        for (int c1 = 0; c1 < n; ++c1) acc = fma(l[c1], w[c1 + n * j], acc);
-      } else {
-        const double* yy = t.base + e * t.pe + y + var * R.Nq;
-        for (int c2 = 0; c2 < n; ++c2) acc = fma(R.L2J[b * n + c2], yy[a + n * c2], acc);
-      }
+      if (z == 0) return Dot{R.l2m, 1, w + j, n, dst};
+      return Dot{z == 1 ? R.l1p : R.l1m, 1, w + n * j, 1, dst};
     }
-    t.base[e * t.pe + out + var * R.Nfn + f] = acc;
-  }
+    const int a = j % n, b = j / n;
+    if (z == 0) return Dot{R.l2m, 1, w + a + n * n * b, n, dst};
+    if (z < 3) return Dot{z == 1 ? R.l1p : R.l1m, 1, w + n * j, 1, dst};
+    return Dot{R.L2J + b * n, 1, t.base + e * t.pe + y + var * R.Nq + a, n, dst};
+  });
   __syncthreads();
 }
 
@@ -408,14 +413,12 @@ __device__ void apply_minv(const DevRef& R, const DevMesh& M, const Tile& t, int
   const int Np = R.Np, Nq = R.Nq;
   if (R.dense_minv) {
     const int tot = t.E * nc * Np;
-    for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+    contract4(tot, Np, [&](int idx) {
       const int i = idx % Np, ev = idx / Np, var = ev % nc, e = ev / nc;
-      const double* Mi = M.minv + (e0 + e) * (int64_t)Np * Np + i;   // column i == row i (symmetric)
-      const double* x = t.base + e * t.pe + in + var * Np;
-      double acc = 0.0;
-      for (int j = 0; j < Np; ++j) acc = fma(Mi[(int64_t)j * Np], x[j], acc);
-      t.base[e * t.pe + out + var * Np + i] = acc;
-    }
+      // column i == row i (symmetric): consecutive threads read consecutive addresses
+      return Dot{M.minv + (e0 + e) * (int64_t)Np * Np + i, Np, t.base + e * t.pe + in + var * Np, 1,
+                 t.base + e * t.pe + out + var * Np + i};
+    });
     __syncthreads();
     return;
   }
