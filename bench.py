@@ -101,6 +101,18 @@ def project_kernel_flops(D, p):
 
 
 # ---------------------------------------------------------------------------------
+def reduce_max(x, device):
+    """Maximum of a per-rank float over all ranks of the default process group (the
+    slowest rank's time); x itself when no group is initialised."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -217,11 +229,7 @@ def run_ours(args):
     ms = ev0.elapsed_time(ev1) / args.steps
     clk = clocks.stop()
     gm.check()
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = reduce_max(ms, dev)
     value = 4.0 * dof * world / (ms * 1e-3)
 
     # ---- dominant kernel (residual) alone, on the launching stream ----
@@ -294,11 +302,7 @@ def run_ours(args):
         e1.record(stream)
     stream.synchronize()
     e2e_ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = reduce_max(e2e_ms, dev)
     nbytes = host_in.numel() * 8
 
     line = {
