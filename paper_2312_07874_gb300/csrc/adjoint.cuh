@@ -34,10 +34,12 @@ __device__ __forceinline__ void load_dir(const double* base, int slot, int T, in
 //           d/da = -(H + 4 f b H'/s)/s^2, d/db = -(H - 4 f a H'/s)/s^2;
 //           direct branch i = (ln b - ln a)/d, d/da = (i - 1/a)/d, d/db = (1/b - i)/d.
 // The beta cotangent goes to (rho, p) through beta = rho/p.
-// Adds (d F/d qL)^T Fb to qL and (d F/d qR)^T Fb to qR, q = (rho, v, p), F = f#(L, R, n).
+// Adds (d F/d qL)^T Fb to qL and (d F/d qR)^T Fb to qR, q = (rho, v, p), F = f#(L, R, n);
+// ipL, ipR = 1/p of the two states.
 template <int D>
 __device__ __forceinline__ void ec_flux_adj(const NodeState<D>& L, const NodeState<D>& R, const double* n,
-                                            double inv_gm1, const double* Fb, double* qL, double* qR) {
+                                            double inv_gm1, const double* Fb, double* qL, double* qR, double ipL,
+                                            double ipR) {
   const unsigned active = __activemask();
   const double s1 = L.rho + R.rho, d1 = R.rho - L.rho;
   const double r1 = rcp_nr<1>(s1), f1 = d1 * r1, u1 = f1 * f1;
@@ -103,7 +105,7 @@ __device__ __forceinline__ void ec_flux_adj(const NodeState<D>& L, const NodeSta
     qR[1 + k] += fma(vnR_b, n[k], fma(vv_b, L.v[k], vs_b));
   }
   // beta = rho / p: d beta/d rho = 1/p, d beta/d p = -beta/p
-  const double gL = ib_b * dia * rcp_nr<2>(L.p), gR = ib_b * dib * rcp_nr<2>(R.p);
+  const double gL = ib_b * dia * ipL, gR = ib_b * dib * ipR;
   qL[0] += fma(rl_b, dra, gL);
   qR[0] += fma(rl_b, drb, gR);
   qL[D + 1] += fma(-gL, L.beta, pL_b);
@@ -116,7 +118,7 @@ template <int D>
 __device__ __forceinline__ void iface_adj(const NodeState<D>& L, const NodeState<D>& R, const double* n,
                                           double inv_gm1, double cL, double cR, int lf, const double* fb,
                                           double* qL, double* qR) {
-  ec_flux_adj<D>(L, R, n, inv_gm1, fb, qL, qR);
+  ec_flux_adj<D>(L, R, n, inv_gm1, fb, qL, qR, rcp_nr<2>(L.p), rcp_nr<2>(R.p));
   if (!lf) return;
   constexpr int NC = D + 2;
   double vnL = 0.0, vnR = 0.0, vvL = 0.0, vvR = 0.0;
@@ -263,9 +265,11 @@ __device__ void apply_RT(const DevRef& R, const Tile& t, int in, int y, int out,
 // and facet nodes (qbar [E][NQ][Ntot]) and, per facet node, the cotangent of the
 // neighbour's state through this element's interface flux (qext [E][NQ][Nfn]).
 struct AdjLayout {
-  int oReg, oM, oS1, oS2, oSv, oSf, oRb, oHb, oQv, oQf, oPart, pe;
+  int oReg, oM, oS1, oS2, oSv, oSf, oIp, oRb, oHb, oQv, oQf, oPart, pe;
   int glob;   // 1: q_b accumulated in the global output instead of shared memory
   int ncol;   // facet-4 columns per pass of the partial sums
+  // oIp: 1/p of every node ([Nq + Nfn] after the states), or -1 where it does not fit
+  // (then computed per pair)
 };
 
 // Shared memory per element of the residual adjoint.  The per-node cotangents q_b are
@@ -279,7 +283,7 @@ constexpr int kAdjSmemBudget = 227 * 1024;
 __host__ __device__ constexpr int facet4_cols(int n) { return n > 10 ? (n + 1) / 2 : n; }
 
 template <int D>
-__host__ __device__ inline AdjLayout adj_layout(int Nq, int Nfn, int Np, int n) {
+__host__ __device__ inline AdjLayout adj_layout_with(int Nq, int Nfn, int Np, int n, bool glob, bool ip) {
   constexpr int NC = D + 2, NF = D + 5, NQ = D + 2;
   AdjLayout L;
   L.oReg = 0;
@@ -288,24 +292,36 @@ __host__ __device__ inline AdjLayout adj_layout(int Nq, int Nfn, int Np, int n) 
   L.oM = 2 * NC * Nq;
   L.oSv = 0;
   L.oSf = NF * Nq;
+  L.oIp = ip ? NF * (Nq + Nfn) : -1;
   int r0 = 2 * NC * Nq + NC * Np;
-  if (NF * (Nq + Nfn) > r0) r0 = NF * (Nq + Nfn);
+  const int rs = (NF + (ip ? 1 : 0)) * (Nq + Nfn);
+  if (rs > r0) r0 = rs;
   L.oRb = r0;
   L.oHb = L.oRb + NC * Nq;
-  L.oQv = L.oHb + NC * Nfn;
-  L.oQf = L.oQv + NQ * Nq;
-  L.oPart = L.oQf + NQ * Nfn;
-  L.ncol = n;
-  L.pe = L.oPart + (D == 3 ? NQ * n * n * n : 0);
-  L.glob = 0;
-  if ((long long)L.pe * 8 > kAdjSmemBudget) {
-    L.glob = 1;
+  L.glob = glob ? 1 : 0;
+  if (!glob) {
+    L.oQv = L.oHb + NC * Nfn;
+    L.oQf = L.oQv + NQ * Nq;
+    L.oPart = L.oQf + NQ * Nfn;
+    L.ncol = n;
+  } else {
     L.oQv = L.oQf = -1;
     L.oPart = L.oHb + NC * Nfn;
     L.ncol = facet4_cols(n);
-    L.pe = L.oPart + (D == 3 ? NQ * n * n * L.ncol : 0);
   }
+  L.pe = L.oPart + (D == 3 ? NQ * n * n * L.ncol : 0);
   return L;
+}
+
+// the first of (q_b in shared memory, with 1/p), (without 1/p), (q_b in global memory,
+// with 1/p), (without) that fits in one CTA
+template <int D>
+__host__ __device__ inline AdjLayout adj_layout(int Nq, int Nfn, int Np, int n) {
+  for (int k = 0; k < 4; ++k) {
+    const AdjLayout L = adj_layout_with<D>(Nq, Nfn, Np, n, k >= 2, (k & 1) == 0);
+    if ((long long)L.pe * 8 <= kAdjSmemBudget || k == 3) return L;
+  }
+  return adj_layout_with<D>(Nq, Nfn, Np, n, true, false);
 }
 
 }  // namespace esd

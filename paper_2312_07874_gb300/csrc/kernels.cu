@@ -112,6 +112,14 @@ __global__ void residual_adjoint_kernel(DevRef R, DevMesh M, int epc, const doub
     else
       sm[e * pe + Ly.oSf + f * Nfn + (k - Nq)] = val;
   }
+  __syncthreads();
+  // 1/p at every node, once, where the layout has room for it (else per pair)
+  if (Ly.oIp >= 0)
+    for (int idx = threadIdx.x; idx < E * Ntot; idx += blockDim.x) {
+      const int e = idx / Ntot, k = idx % Ntot;
+      const double pk = k < Nq ? sm[e * pe + Ly.oSv + (D + 1) * Nq + k] : sm[e * pe + Ly.oSf + (D + 1) * Nfn + (k - Nq)];
+      sm[e * pe + Ly.oIp + k] = rcp_nr<2>(pk);
+    }
   // q_b of element e: volume node v of variable c at qv_e[c * qvs + v], facet node f at
   // qf_e[c * qfs + f] (shared memory, or the global output itself when it does not fit)
   const int qvs = Ly.glob ? Ntot : Nq, qfs = Ly.glob ? Ntot : Nfn;
@@ -165,6 +173,10 @@ __global__ void residual_adjoint_kernel(DevRef R, DevMesh M, int epc, const doub
   const double* hb = sm + el * pe + Ly.oHb;
   double* qv = active ? qv_of(el) : nullptr;
   double* qf = active ? qf_of(el) : nullptr;
+  const double* ipn = sm + el * pe + (Ly.oIp >= 0 ? Ly.oIp : 0);   // [Nq volume | Nfn facet]
+  const bool have_ip = Ly.oIp >= 0;
+  auto ip_v = [&](const NodeState<D>& S, int v) { return have_ip ? ipn[v] : rcp_nr<2>(S.p); };
+  auto ip_f = [&](const NodeState<D>& S, int f) { return have_ip ? ipn[Nq + f] : rcp_nr<2>(S.p); };
   for (int ph = 0; ph < D; ++ph) {
     if (active) {
       int base, stride;
@@ -191,7 +203,7 @@ __global__ void residual_adjoint_kernel(DevRef R, DevMesh M, int epc, const doub
             qa[c] = 0.0;
             qb[c] = 0.0;
           }
-          ec_flux_adj<D>(Si, Sj, nn, inv_gm1, Fb, qa, qb);
+          ec_flux_adj<D>(Si, Sj, nn, inv_gm1, Fb, qa, qb, ip_v(Si, vi), ip_v(Sj, vj));
 #pragma unroll
           for (int c = 0; c < NQ; ++c) {
             qv[c * qvs + vi] += qa[c];
@@ -201,6 +213,7 @@ __global__ void residual_adjoint_kernel(DevRef R, DevMesh M, int epc, const doub
       }
       auto facet_pairs = [&](const double* fd, int slot0, int f, int cnt) {
         NodeState<D> Sfj = load_state<D>(Sf, Nfn, f);
+        const double ipj = ip_f(Sfj, f);
         double acc[NQ];
 #pragma unroll
         for (int c = 0; c < NQ; ++c) acc[c] = 0.0;
@@ -214,7 +227,7 @@ __global__ void residual_adjoint_kernel(DevRef R, DevMesh M, int epc, const doub
             Fb[c] = -rb[c * Nq + vi] - hb[c * Nfn + f];
             qa[c] = 0.0;
           }
-          ec_flux_adj<D>(Si, Sfj, nn, inv_gm1, Fb, qa, acc);
+          ec_flux_adj<D>(Si, Sfj, nn, inv_gm1, Fb, qa, acc, ip_v(Si, vi), ipj);
 #pragma unroll
           for (int c = 0; c < NQ; ++c) qv[c * qvs + vi] += qa[c];
         }
@@ -242,6 +255,7 @@ __global__ void residual_adjoint_kernel(DevRef R, DevMesh M, int epc, const doub
         int m = bp * n;
         const int f = 3 * Nqf + a + n * bp;
         NodeState<D> Sfj = load_state<D>(Sf, Nfn, f);
+        const double ipj = ip_f(Sfj, f);
         double acc[NQ];
 #pragma unroll
         for (int c = 0; c < NQ; ++c) acc[c] = 0.0;
@@ -255,7 +269,7 @@ __global__ void residual_adjoint_kernel(DevRef R, DevMesh M, int epc, const doub
             Fb[c] = -rb[c * Nq + vi] - hb[c * Nfn + f];
             qa[c] = 0.0;
           }
-          ec_flux_adj<D>(Si, Sfj, nn, inv_gm1, Fb, qa, acc);
+          ec_flux_adj<D>(Si, Sfj, nn, inv_gm1, Fb, qa, acc, ip_v(Si, vi), ipj);
 #pragma unroll
           for (int c = 0; c < NQ; ++c) qv[c * qvs + vi] += qa[c];
         }
