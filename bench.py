@@ -424,18 +424,21 @@ def run_reference(args):
 # ---------------------------------------------------------------------------------
 # batched execution: 64 independent meshes, one persistent launch per kernel and degree
 # ---------------------------------------------------------------------------------
-def batch_mix(seed=5, n=64):
+def batch_mix(seed=5, n=64, small=False):
     """Seeded mix: triangles on uniform 2D grids (2 M^2 in [200, 20000]), tetrahedra from
     uniform cube splits (6 M^3 in [384, 24576]), p uniform in {2..10} for both, vortex or
-    Taylor-Green states (about 110 GB of device memory in total)."""
+    Taylor-Green states (about 110 GB of device memory in total).  small=True: the same
+    recipe with small meshes only (triangles M in [10, 30], tetrahedra M in [3, 6]), where
+    launch overheads are a visible part of a step."""
     rng = np.random.default_rng(seed)
+    tri_m, tet_m = ((10, 31), (3, 7)) if small else ((10, 101), (4, 17))
     mix = []
     for i in range(n):
         if i % 2 == 0:
-            M = int(rng.integers(10, 101))
+            M = int(rng.integers(*tri_m))
             mix.append((2, M, int(rng.integers(2, 11)), "vortex"))
         else:
-            M = int(rng.integers(4, 17))
+            M = int(rng.integers(*tet_m))
             mix.append((3, M, int(rng.integers(2, 11)), "tgv"))
     return mix
 
@@ -446,7 +449,8 @@ def run_batch(args):
     dev = torch.device("cuda", 0)
     meshes, states, dts, dof = [], [], [], 0
     t0 = time.time()
-    for dim, M, p, state in batch_mix():
+    mix = batch_mix(small=args.batch_small)
+    for dim, M, p, state in mix:
         L = 2 * np.pi
         mesh, X = I.config_mesh(dim, M, L, p, True)
         gm = E.Mesh(dim, p, X, mesh.nbr_elem, mesh.nbr_face)
@@ -486,7 +490,8 @@ def run_batch(args):
             "plain_per_mesh": {"value": 4.0 * dof / (ms_plain * 1e-3), "ms_per_step": ms_plain,
                                "launches_per_step": 8 * len(meshes)},
             "speedup": ms_plain / ms_batch, "n_meshes": len(meshes), "dof": dof,
-            "mix": [f"{'tri' if d == 2 else 'tet'} M={M} p={p}" for d, M, p, _ in batch_mix()],
+            "mix": [f"{'tri' if d == 2 else 'tet'} M={M} p={p}" for d, M, p, _ in mix],
+            "meshes": "small (launch-bound)" if args.batch_small else "batching workload",
             "setup_s": setup_s, "steps": args.steps, "warmup": args.warmup}
     print(json.dumps(line), flush=True)
     E.esd_batch_destroy(b)
@@ -604,6 +609,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="0 skips the CPU baseline")
     ap.add_argument("--mesh-m", type=int, default=16, help="cells per direction (16 = the benchmark)")
     ap.add_argument("--batch", action="store_true", help="64-mesh batched vs per-mesh comparison")
+    ap.add_argument("--batch-small", action="store_true", help="with --batch: 64 small meshes instead")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes (profiling)")
     ap.add_argument("--sweep", action="store_true", help="per-degree throughput of the triangle and "
                     "tetrahedron workloads and the differentiation workload (one line each)")

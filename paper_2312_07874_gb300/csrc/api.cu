@@ -579,27 +579,56 @@ static esd_status batch_run(esd_batch b, int kind, const std::vector<const doubl
     cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking);
     cs = own;
   }
-  cudaGraph_t graph;
-  if ((e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal))) return cuda_fail(e, "batch capture");
-  const int nst = kind == 0 ? 1 : 4;
-  size_t tix = 0;
+  // The groups (one per dimension and degree) share no data: each group's stages form
+  // one chain on its own forked stream, so the graph runs the groups concurrently and the
+  // tail of one group's launch overlaps the work of the others.
+  const size_t ng = b->groups.size();
+  std::vector<cudaStream_t> gs(ng, nullptr);
+  std::vector<cudaEvent_t> ev(ng + 1, nullptr);
   cudaError_t e1 = cudaSuccess;
-  for (int st = 0; st < nst && !e1; ++st)
-    for (auto& g : b->groups) {
-      BatchMesh* tab = G.d_tables[tix++];
+  for (size_t gi = 0; gi < ng && !e1; ++gi) e1 = cudaStreamCreateWithFlags(&gs[gi], cudaStreamNonBlocking);
+  for (size_t k = 0; k <= ng && !e1; ++k) e1 = cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming);
+  auto release = [&] {
+    for (auto x : gs)
+      if (x) cudaStreamDestroy(x);
+    for (auto x : ev)
+      if (x) cudaEventDestroy(x);
+    if (own) cudaStreamDestroy(own);
+  };
+  if (e1) {
+    release();
+    return cuda_fail(e1, "batch streams");
+  }
+  cudaGraph_t graph;
+  if ((e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal))) {
+    release();
+    return cuda_fail(e, "batch capture");
+  }
+  const int nst = kind == 0 ? 1 : 4;
+  e1 = cudaEventRecord(ev[ng], cs);
+  for (size_t gi = 0; gi < ng && !e1; ++gi) {
+    const BatchGroup& g = b->groups[gi];
+    if ((e1 = cudaStreamWaitEvent(gs[gi], ev[ng], 0))) break;
+    for (int st = 0; st < nst && !e1; ++st) {
+      BatchMesh* tab = G.d_tables[st * ng + gi];
       if ((e1 = launch_batch(g.dim, g.p + 1, 0, tab, g.d_pitems, (int)g.pitems.size(), g.pgrid, g.pthreads,
-                             g.psmem, cs)))
+                             g.psmem, gs[gi])))
         break;
-      if ((e1 = launch_batch(g.dim, g.p + 1, 1, tab, g.d_ritems, (int)g.ritems.size(), g.rgrid, g.rthreads,
-                             g.rsmem, cs)))
-        break;
+      e1 = launch_batch(g.dim, g.p + 1, 1, tab, g.d_ritems, (int)g.ritems.size(), g.rgrid, g.rthreads, g.rsmem,
+                        gs[gi]);
     }
+    if (!e1) e1 = cudaEventRecord(ev[gi], gs[gi]);
+    if (!e1) e1 = cudaStreamWaitEvent(cs, ev[gi], 0);
+  }
   e = cudaStreamEndCapture(cs, &graph);
-  if (e1) return cuda_fail(e1, "batch launch");
-  if (e) return cuda_fail(e, "batch end capture");
+  if (e1 || e) {
+    if (!e) cudaGraphDestroy(graph);
+    release();
+    return e1 ? cuda_fail(e1, "batch launch") : cuda_fail(e, "batch end capture");
+  }
   e = cudaGraphInstantiate(&G.exec, graph, 0);
   cudaGraphDestroy(graph);
-  if (own) cudaStreamDestroy(own);
+  release();
   if (e) return cuda_fail(e, "batch graph instantiate");
   b->graphs.push_back(G);
   e = cudaGraphLaunch(G.exec, s);

@@ -63,6 +63,24 @@ def test_batch_rk_step_equals_per_mesh():
     E.esd_batch_destroy(b)
 
 
+def test_autotune_subset_and_invalid_bits():
+    import torch
+    import paper_2312_07874_gb300 as E
+    ms = _meshes()
+    m, u = ms[4]
+    before = m.rhs(u)
+    info0 = dict(m.info)
+    m.autotune(u, E.ESD_TUNE_ADJOINT)        # the forward shapes stay as they were
+    assert m.info["elems_per_cta_residual"] == info0["elems_per_cta_residual"]
+    assert m.info["elems_per_cta_project"] == info0["elems_per_cta_project"]
+    with pytest.raises(E.EsdError) as ex:
+        m.autotune(u, 8)
+    assert ex.value.status == -1
+    after = m.rhs(u)
+    torch.cuda.synchronize()
+    assert torch.equal(before, after)
+
+
 def test_autotune_keeps_results_and_valid_shapes():
     import torch
     import paper_2312_07874_gb300 as E
