@@ -600,6 +600,39 @@ def run_sweep(args):
                       "l2": "flushed (256 MB write) before every timed call", "dtype": "f64"}), flush=True)
 
 
+def run_diagnostics_series(args):
+    """Conservation and entropy over a run: Taylor-Green vortex at Mach 0.1 on 4^3 x 6 = 384
+    curved tetrahedra, p = 4, entropy-conservative (EC) and Lax-Friedrichs (LF) interface
+    fluxes, RK4 at CFL 0.1, totals and rates sampled every 10 steps (one line per flux)."""
+    import torch
+    import paper_2312_07874_gb300 as E
+    L, M, p = 2 * np.pi, 4, 4
+    mesh, X = I.config_mesh(3, M, L, p, True)
+    lam = I.max_wave_speed_sampled(lambda y: I.taylor_green(y, 0.1), 3, L)
+    dt = 0.1 * (L / M) / (lam * (2 * p + 1))
+    n_steps = max(20, args.steps) if args.steps != 10 else 200
+    for flux in ("EC", "LF"):
+        gm = E.Mesh(3, p, X, mesh.nbr_elem, mesh.nbr_face, flux=flux)
+        x = gm.volume_nodes()
+        un = np.ascontiguousarray(np.transpose(I.taylor_green(x, 0.1), (0, 2, 1)))
+        u = gm.l2_project(torch.from_numpy(un).cuda())
+        t0 = time.time()
+        steps, tot, rates = gm.run_diagnostics(u, dt, n_steps, every=10)
+        wall = time.time() - t0
+        nc = 5
+        cons = np.abs(tot[:, :nc] - tot[0, :nc]).max(axis=0) / np.abs(tot[0, :nc]).max()
+        ent_rate = rates[:, nc] / rates[:, nc + 1]
+        S = tot[:, nc]
+        print(json.dumps({"kind": "diagnostics", "workload": f"tet_tgv_curved p={p} M={M} (384 tets), {flux} facets",
+                          "steps": int(steps[-1]), "dt": dt, "t_final": float(steps[-1] * dt),
+                          "samples": int(len(steps)),
+                          "max_conserved_drift_rel": cons.tolist(),
+                          "entropy_rate_rel": {"min": float(ent_rate.min()), "max": float(ent_rate.max())},
+                          "entropy_total_change_rel": float((S[-1] - S[0]) / abs(S[0])),
+                          "entropy_monotone": bool(np.all(np.diff(S) <= 1e-12 * abs(S[0]))),
+                          "wall_s": wall}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -611,6 +644,7 @@ def main():
     ap.add_argument("--batch", action="store_true", help="64-mesh batched vs per-mesh comparison")
     ap.add_argument("--batch-small", action="store_true", help="with --batch: 64 small meshes instead")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes (profiling)")
+    ap.add_argument("--diagnostics", action="store_true", help="conservation / entropy time series (EC and LF)")
     ap.add_argument("--sweep", action="store_true", help="per-degree throughput of the triangle and "
                     "tetrahedron workloads and the differentiation workload (one line each)")
     args = ap.parse_args()
@@ -620,6 +654,9 @@ def main():
         return
     if args.sweep:
         run_sweep(args)
+        return
+    if args.diagnostics:
+        run_diagnostics_series(args)
         return
     if args.warmup < 3:
         args.warmup = 3

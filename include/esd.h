@@ -174,6 +174,15 @@ esd_status esd_rk_step_vjp(esd_mesh mesh, const double* stage_ckpt, double dt, c
  * sum |w_i r_i| as its scale. */
 esd_status esd_diagnostics(esd_mesh mesh, const double* u, double* out, void* stream);
 
+/* Totals over the mesh of the state u (device [n_elem][N_c][N_p*]): out (device, N_c + 1
+ * doubles) receives sum_kappa 1^T W J V u~ for each conserved variable (the quantities
+ * Theorem 2 conserves; constant over RK steps up to rounding on periodic meshes), then
+ * sum_kappa 1^T W J S(V u~), the total of the entropy function S = -rho s / (gamma - 1),
+ * s = ln(p / rho^gamma) (Section 7.1; constant in time for ESD_FLUX_EC up to the time
+ * integration error, non-increasing for ESD_FLUX_LF).  Quadrature of the mass matrix
+ * (interpolated J).  Used for conservation and entropy time series over a run. */
+esd_status esd_integrals(esd_mesh mesh, const double* u, double* out, void* stream);
+
 /* Batched, persistent execution of many independent meshes (not in the paper).
  * The batch keeps references to the meshes, which must outlive it. */
 esd_status esd_batch_create(const esd_mesh* meshes, int n, esd_batch* out);

@@ -54,6 +54,7 @@ SYMBOLS = {
     "esd_rk_step_vjp": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
                          ctypes.c_void_p], ctypes.c_int),
     "esd_diagnostics": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "esd_integrals": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
     "esd_batch_create": ([ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
     "esd_batch_destroy": ([ctypes.c_void_p], ctypes.c_int),
     "esd_batch_rhs": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
@@ -209,6 +210,10 @@ def esd_diagnostics(h, u, out, stream=None):
     _check(lib().esd_diagnostics(h, _ptr(u), _ptr(out), _stream(stream)))
 
 
+def esd_integrals(h, u, out, stream=None):
+    _check(lib().esd_integrals(h, _ptr(u), _ptr(out), _stream(stream)))
+
+
 ESD_TUNE_PROJECT, ESD_TUNE_RESIDUAL, ESD_TUNE_ADJOINT, ESD_TUNE_ALL = 1, 2, 4, 7
 
 
@@ -320,6 +325,34 @@ class Mesh:
         out = torch.empty(self.nc + 2, dtype=torch.float64, device="cuda")
         esd_diagnostics(self.handle, u, out)
         return out
+
+    def integrals(self, u):
+        """[N_c + 1]: totals of the conserved variables, then of the entropy function."""
+        import torch
+        out = torch.empty(self.nc + 1, dtype=torch.float64, device="cuda")
+        esd_integrals(self.handle, u, out)
+        return out
+
+    def run_diagnostics(self, u, dt, n_steps, every=1):
+        """Advance u in place by n_steps RK4 steps, sampling before the first step and
+        after every `every` steps the totals (esd_integrals) and the rates (esd_diagnostics):
+        returns (steps [K], totals [K, N_c + 1], rates [K, N_c + 2]) as numpy arrays."""
+        import numpy as np
+        import torch
+        steps, tot, rates = [], [], []
+
+        def sample(k):
+            steps.append(k)
+            tot.append(self.integrals(u))
+            rates.append(self.diagnostics(u))
+        sample(0)
+        for k in range(1, n_steps + 1):
+            self.rk_step(u, dt)
+            if k % every == 0 or k == n_steps:
+                sample(k)
+        torch.cuda.synchronize()
+        self.check()
+        return (np.array(steps), torch.stack(tot).cpu().numpy(), torch.stack(rates).cpu().numpy())
 
     def check(self):
         esd_mesh_check(self.handle)

@@ -374,6 +374,17 @@ esd_status esd_diagnostics(esd_mesh m, const double* u, double* out, void* strea
   return e ? cuda_fail(e, "reduce launch") : ESD_OK;
 }
 
+esd_status esd_integrals(esd_mesh m, const double* u, double* out, void* stream) {
+  if (!m) return fail(ESD_ERR_ARG, "null mesh");
+  esd_status st;
+  if ((st = check_dev(u, "u")) || (st = check_dev(out, "out"))) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = launch_integrals(m->R, m->M, m->L, u, m->ws_diag, s);
+  if (e) return cuda_fail(e, "integrals launch");
+  e = launch_reduce_diag(m->ws_diag, m->E, m->nc + 1, out, s);
+  return e ? cuda_fail(e, "reduce launch") : ESD_OK;
+}
+
 esd_status esd_rhs_vjp(esd_mesh m, const double* u, const double* cot, double* grad, void* stream) {
   if (!m) return fail(ESD_ERR_ARG, "null mesh");
   esd_status st;

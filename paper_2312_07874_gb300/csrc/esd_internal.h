@@ -167,6 +167,8 @@ cudaError_t launch_residual_batch_d3_hi(int n, const BatchMesh* meshes, const Ba
                                         int grid, int threads, size_t smem, cudaStream_t s);
 cudaError_t set_residual_smem_d3_hi(int lim);
 cudaError_t launch_reduce_diag(const double* part, int64_t E, int ncol, double* out, cudaStream_t s);
+cudaError_t launch_integrals(const DevRef& R, const DevMesh& M, const LaunchCfg& L, const double* u, double* part,
+                             cudaStream_t s);
 cudaError_t launch_copy(const double* src, double* dst, int64_t n, cudaStream_t s);
 cudaError_t measure_fp64(double* flops, cudaStream_t s);
 cudaError_t launch_staging_timeout_probe(int* flag, double seconds, cudaStream_t s);

@@ -31,6 +31,60 @@ __global__ void project_kernel(DevRef R, DevMesh M, int epc, const double* __res
 }
 
 // ---------------------------------------------------------------------------
+// Volume integrals of the conserved variables and of the entropy function
+// S(u) = -rho s / (gamma - 1), s = ln(p / rho^gamma) (Section 7.1), with the quadrature of
+// the mass matrix (W J, interpolated J): per element sum_i (W J)_i u_i and
+// sum_i (W J)_i S(u_i) at the volume nodes, u = V u~.  part: [E][N_c + 1].
+// ---------------------------------------------------------------------------
+template <int D>
+__global__ void integrals_kernel(DevRef R, DevMesh M, int epc, const double* __restrict__ u,
+                                 double* __restrict__ part) {
+  extern __shared__ double sm[];
+  constexpr int NC = D + 2;
+  const int Np = R.Np, Nq = R.Nq;
+  const int oM = 0, oA = NC * Np, oB = oA + NC * Nq, oC = oB + NC * Nq;
+  const int pe = oC + NC * Nq;
+  const int64_t e0 = (int64_t)blockIdx.x * epc;
+  const int E = (int)((M.E - e0) < (int64_t)epc ? (M.E - e0) : (int64_t)epc);
+  Tile t{sm, pe, E};
+  for (int idx = threadIdx.x; idx < E * NC * Np; idx += blockDim.x) {
+    const int e = idx / (NC * Np), r = idx % (NC * Np);
+    sm[e * pe + oM + r] = u[(e0 + e) * NC * Np + r];
+  }
+  __syncthreads();
+  apply_V<D>(R, t, oM, oB, oC, oA, NC);
+  const double gamma = M.gamma, inv_gm1 = 1.0 / (gamma - 1.0);
+  const int lane = threadIdx.x % 32, nw = blockDim.x / 32;
+  for (int e = threadIdx.x / 32; e < E; e += nw) {
+    double acc[NC + 1];
+#pragma unroll
+    for (int c = 0; c <= NC; ++c) acc[c] = 0.0;
+    for (int v = lane; v < Nq; v += 32) {
+      const double wj = M.wj[(e0 + e) * Nq + v];
+      double uc[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        uc[c] = sm[e * pe + oA + c * Nq + v];
+        acc[c] = fma(wj, uc[c], acc[c]);
+      }
+      double vv = 0.0;
+#pragma unroll
+      for (int k = 0; k < D; ++k) vv = fma(uc[1 + k], uc[1 + k], vv);
+      const double rho = uc[0];
+      const double p = (gamma - 1.0) * (uc[D + 1] - 0.5 * vv * rcp_nr<2>(rho));
+      const double sent = log_tab(p, R.mtab) - gamma * log_tab(rho, R.mtab);
+      acc[NC] = fma(wj, -rho * sent * inv_gm1, acc[NC]);
+    }
+#pragma unroll
+    for (int c = 0; c <= NC; ++c) {
+      double x = acc[c];
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      if (lane == 0) part[(e0 + e) * (NC + 1) + c] = x;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Batched execution of many meshes (one launch per kernel and dimension): a
 // persistent grid walks a list of (mesh, element tile) items; each item runs the
 // same tile code with that mesh's tables, layout and epilogue.
@@ -516,6 +570,8 @@ cudaError_t set_smem_limits(const LaunchCfg& L, int dim) {
     if (e) return e;
     e = cudaFuncSetAttribute(project_batch_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     if (e) return e;
+    e = cudaFuncSetAttribute(integrals_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    if (e) return e;
     e = set_residual_smem_d2(lim);
   } else {
     e = cudaFuncSetAttribute(project_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
@@ -527,6 +583,8 @@ cudaError_t set_smem_limits(const LaunchCfg& L, int dim) {
     e = cudaFuncSetAttribute(project_adjoint_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     if (e) return e;
     e = cudaFuncSetAttribute(project_batch_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    if (e) return e;
+    e = cudaFuncSetAttribute(integrals_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     if (e) return e;
     e = set_residual_smem_d3(lim);
   }
@@ -601,6 +659,20 @@ cudaError_t launch_batch(int dim, int n, int stage, const BatchMesh* meshes, con
   }
   return dim == 2 ? launch_residual_batch_d2(n, meshes, items, nitems, grid, threads, smem, s)
                   : launch_residual_batch_d3(n, meshes, items, nitems, grid, threads, smem, s);
+}
+
+cudaError_t launch_integrals(const DevRef& R, const DevMesh& M, const LaunchCfg& L, const double* u, double* part,
+                             cudaStream_t s) {
+  // same shared footprint as the projection tile without its facet block
+  const unsigned grid = (unsigned)((M.E + L.ea - 1) / L.ea);
+  const int nc = R.dim + 2;
+  const size_t smem = (size_t)L.ea * nc * (R.Np + 3 * R.Nq) * sizeof(double);
+  const int threads = L.ta < 64 ? 64 : L.ta;
+  if (R.dim == 2)
+    integrals_kernel<2><<<grid, threads, smem, s>>>(R, M, L.ea, u, part);
+  else
+    integrals_kernel<3><<<grid, threads, smem, s>>>(R, M, L.ea, u, part);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_reduce_diag(const double* part, int64_t E, int ncol, double* out, cudaStream_t s) {
