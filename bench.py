@@ -397,7 +397,7 @@ def run_reference(args):
     if rank != 0:
         return
     D, um = _oracle_setup()
-    n_el = 32
+    n_el = min(512, D.E)   # ~1 s of oracle work per step on one core; amortises the per-call setup
     times = []
     for _ in range(args.warmup):
         _oracle_sample(D, um, n_el)
@@ -412,7 +412,7 @@ def run_reference(args):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded analytic TGV state, no dataset)",
         "impl": "reference",
         "config": {"workload": "tet_tgv_curved p=4: periodic [0,2pi]^3, 16^3x6 = 24576 curved tets, TGV Ma=0.1, "
-                               "LF interface flux (oracle: one d u~/dt of a 32-element sample per step)",
+                               "LF interface flux (oracle: one d u~/dt of a 512-element sample per step)",
                    "n_elem": D.E, "p": WORKLOAD["p"]},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"{n_el} elements per step, sparse route"},
