@@ -217,3 +217,13 @@ def test_invalid_meshes_rejected():
     with pytest.raises(E.EsdError) as ex:
         E.esd_debug_host_setup(3, 11, I.config_mesh(3, 3, 1.0, 1, False)[1], mesh.nbr_elem, mesh.nbr_face)
     assert ex.value.status in (-1, -7)
+
+
+def test_empty_mesh_rejected():
+    import paper_2312_07874_gb300 as E
+    with pytest.raises(E.EsdError) as ex:
+        E.esd_debug_host_setup(3, 2, np.zeros((0, 10, 3)), np.zeros((0, 4), np.int32), np.zeros((0, 4), np.int8))
+    assert ex.value.status == -1
+    with pytest.raises(E.EsdError) as ex:
+        E.esd_debug_host_setup(2, 2, np.zeros((0, 6, 2)), np.zeros((0, 3), np.int32), np.zeros((0, 3), np.int8))
+    assert ex.value.status == -1
