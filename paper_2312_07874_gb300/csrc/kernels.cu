@@ -536,8 +536,9 @@ LaunchCfg choose_launch(const RefTables& r) {
   L.tb = std::max(64, ((best * r.T + 31) / 32) * 32);
   L.sb = smem_residual(r, best);
   // residual adjoint: same task structure, larger shared footprint
+  // (the adjoint kernel uses up to 128 registers per thread: at most 512 threads per block)
   int evmax = std::max(1, (int)(kSmemBudget / smem_residual_adj(r, 1)));
-  evmax = std::min(evmax, 1024 / r.T);
+  evmax = std::min(evmax, std::max(1, 512 / r.T));
   best = 1;
   best_score = -1.0;
   for (int e = 1; e <= evmax; ++e) {
