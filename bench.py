@@ -143,7 +143,10 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        # the raw samples go to a scratch file (BENCH_CLOCKS_DIR, default the system temp dir)
+        import tempfile
+        d = os.environ.get("BENCH_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(d, f"esd_bench_clocks_rank{index}.csv")
 
     def start(self):
         try:
