@@ -46,7 +46,7 @@ typedef enum {
   ESD_ERR_STATE = -4,       /* non-admissible state seen by a kernel (rho <= 0, p <= 0, NaN/Inf) */
   ESD_ERR_TIMEOUT = -5,     /* a bounded device-side wait gave up */
   ESD_ERR_NOMEM = -6,       /* device allocation failed at create time */
-  ESD_ERR_UNSUPPORTED = -7  /* degree or size outside what this build supports */
+  ESD_ERR_UNSUPPORTED = -7  /* degree or size outside what the library supports */
 } esd_status;
 
 enum { ESD_FLUX_EC = 0, ESD_FLUX_LF = 1 };

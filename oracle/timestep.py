@@ -1,5 +1,5 @@
 """Classical four-stage Runge-Kutta step (the paper integrates with an
-eighth-order Dormand-Prince method; this build steps with RK4).
+eighth-order Dormand-Prince method; the library steps with RK4).
 Oracle (test infrastructure only)."""
 
 

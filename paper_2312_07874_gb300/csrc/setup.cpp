@@ -409,7 +409,7 @@ esd_status build_ref(int dim, int p, RefTables* R, std::string* err) {
                             : (long)r.Np * n + (long)r.S12 * n * n + (long)r.Nq * (p + 1);
     r.dense_minv = (long)r.Np * r.Np <= 2 * V + r.Nq ? 1 : 0;
   }
-  // facet pair phases (see kernels.cu for the task structure)
+  // facet pair phases (the line-task structure of device.cuh: line_task)
   if (dim == 2) {
     r.fph_len[0] = 2 * n;  // faces 2 and 3 along eta1-lines
     r.fph_len[1] = n;      // face 1 along eta2-lines
