@@ -1,5 +1,6 @@
 // Internal declarations shared by the host setup (setup.cpp), the kernels
-// (kernels.cu) and the C ABI (api.cu).  Not part of the public interface.
+// (kernels.cu, residual_d*.cu and the device headers) and the C ABI (api.cu).  Not part of
+// the public interface.
 #pragma once
 
 #include <cstdint>

@@ -651,7 +651,7 @@ esd_status build_host_mesh(const esd_mesh_desc& d, HostMesh* H, std::string* err
                 double S = 0.5 * (Qij - Qji);
                 for (int mm = 0; mm < dim; ++mm) nij[mm] += S * (G[vi * 9 + l * 3 + mm] + G[vj * 9 + l * 3 + mm]);
               }
-              // stored halved: the kernels use n/2 (see kernels.cu, ec_flux_fast)
+              // stored halved: the kernels use n/2 (device.cuh, ec_flux_fast)
               for (int mm = 0; mm < dim; ++mm) vd[((size_t)(ph * r.Lv + m) * dim + mm) * T + t] = 0.5 * nij[mm];
             }
         }
