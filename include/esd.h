@@ -16,7 +16,8 @@
  * - Device arrays must be allocated by the caller (cudaMalloc or a framework
  *   allocator), be 8-byte aligned, and stay alive until the stream work that
  *   uses them completes.  The library never allocates or frees memory in the
- *   per-step calls; everything it needs is allocated by esd_mesh_create.
+ *   per-step calls; everything it needs is allocated by esd_mesh_create (the batch
+ *   calls allocate their small per-launch tables once per new set of arguments).
  * - "stream" is a cudaStream_t passed as void*; NULL is the legacy default
  *   stream.  All device calls are asynchronous on that stream; a returned
  *   ESD_OK means the work was enqueued.
