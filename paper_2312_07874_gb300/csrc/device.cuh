@@ -1,6 +1,7 @@
 // Device-side building blocks shared by the kernel translation units: per-node
-// states, the two-point flux, sum-factorised transforms, the projection and
-// residual tiles, and the adjoint pieces.  Internal to the library.
+// states, the two-point flux, table-driven log/exp, sum-factorised transforms, the
+// projection and residual tiles (the adjoint pieces are in adjoint.cuh).  Internal to
+// the library.
 #pragma once
 
 #include <cmath>
@@ -32,47 +33,11 @@ __device__ __forceinline__ NodeState<D> load_state(const double* S, int stride, 
   return s;
 }
 
-// {{a}}_ln with per-node logarithms: for u = ((b-a)/(b+a))^2 < 1e-4 the series of
-// ln(b/a) = 2 artanh((b-a)/(b+a)) gives (a+b)/(2 + 2u/3 + 2u^2/5 + 2u^3/7);
-// otherwise (b-a)/(ln b - ln a).
-__device__ __forceinline__ double log_mean(double a, double b, double la, double lb) {
-  double s = a + b, d = b - a;
-  double f = d / s, u = f * f;
-  if (u < 1.0e-4) return s / (2.0 + u * (2.0 / 3.0 + u * (2.0 / 5.0 + u * (2.0 / 7.0))));
-  return d / (lb - la);
-}
-
-__device__ __forceinline__ double inv_log_mean(double a, double b, double la, double lb) {
-  double s = a + b, d = b - a;
-  double f = d / s, u = f * f;
-  if (u < 1.0e-4) return (2.0 + u * (2.0 / 3.0 + u * (2.0 / 5.0 + u * (2.0 / 7.0)))) / s;
-  return (lb - la) / d;
-}
-
-// Directional entropy-conservative flux f#(U^-,U^+,n) = sum_m n_m f_m^# (Eq. (ranocha_flux));
-// the energy component uses rho_ln {{v}}.n (v^-.v^+/2 + 1/((gamma-1){{rho/p}}_ln)) + (p^- v^+.n + p^+ v^-.n)/2.
-template <int D>
-__device__ __forceinline__ void ec_flux(const NodeState<D>& L, const NodeState<D>& R, const double* n,
-                                        double inv_gm1, double* F) {
-  double rho_ln = log_mean(L.rho, R.rho, L.lrho, R.lrho);
-  double ib_ln = inv_log_mean(L.beta, R.beta, L.lbeta, R.lbeta);
-  double vnL = 0.0, vnR = 0.0, vv = 0.0;
-#pragma unroll
-  for (int k = 0; k < D; ++k) {
-    vnL = fma(n[k], L.v[k], vnL);
-    vnR = fma(n[k], R.v[k], vnR);
-    vv = fma(L.v[k], R.v[k], vv);
-  }
-  double frho = rho_ln * 0.5 * (vnL + vnR);
-  double pavg = 0.5 * (L.p + R.p);
-  F[0] = frho;
-#pragma unroll
-  for (int k = 0; k < D; ++k) F[1 + k] = fma(frho, 0.5 * (L.v[k] + R.v[k]), pavg * n[k]);
-  F[D + 1] = fma(frho, fma(0.5, vv, inv_gm1 * ib_ln), 0.5 * (L.p * vnR + R.p * vnL));
-}
-
 // ---------------------------------------------------------------------------
-// FP64-lean evaluation of the same flux for the pair loops.
+// The directional entropy-conservative flux f#(U^-, U^+, n) = sum_m n_m f_m^#
+// (Eq. (ranocha_flux), reading R4: the energy component is
+// rho_ln {{v}}.n (v^-.v^+/2 + 1/((gamma-1) {{rho/p}}_ln)) + (p^- v^+.n + p^+ v^-.n)/2),
+// evaluated FP64-lean for the pair loops:
 //
 // * Reciprocals come from the MUFU approximation (rcp.approx.ftz.f64, another pipe)
 //   refined by Newton-Raphson steps x <- x + x (1 - a x), each of which squares the
@@ -80,6 +45,9 @@ __device__ __forceinline__ void ec_flux(const NodeState<D>& L, const NodeState<D
 //   correction, two steps give full double precision.
 // * The log-mean branch is chosen by an integer comparison of the bit patterns of
 //   u >= 0 and 1e-4 (same decision as the floating-point comparison, off the FP64 pipe).
+// * Logarithmic means {{a}}_ln = (b-a)/(ln b - ln a) use the per-node logarithms; for
+//   u = f^2 < 1e-4, f = (b-a)/(b+a), the series of ln(b/a) = 2 artanh f gives
+//   {{a}}_ln = (a+b)/(2F(u)), F(u) = artanh(f)/f = 1 + u/3 + u^2/5 + u^3/7 + ...
 // * In the series branch, rho_ln = (a+b) G(u) with G = 1/(2F(u)) expanded to the same
 //   order, G = 1/2 - u/6 - 2u^2/45 - 22u^3/945 (differs from (a+b)/(2F) by < 1e-17
 //   relative for u < 1e-4); 1/((gamma-1) beta_ln) = K(u)/(a+b) with K = 2F/(gamma-1).
