@@ -505,7 +505,8 @@ def run_batch(args):
 # roofline fraction (not the headline line; one JSON line per configuration)
 # ---------------------------------------------------------------------------------
 SWEEP = ([("tri_vortex_curved", 2, 64, 1.0, p, "vortex") for p in (4, 6, 8, 10)]
-         + [("tet_tgv_curved", 3, 16, 2 * np.pi, p, "tgv") for p in (2, 4, 6)])
+         + [("tet_tgv_curved", 3, 16, 2 * np.pi, p, "tgv") for p in (2, 4, 6)]
+         + [("tet_tgv_curved_8", 3, 8, 2 * np.pi, p, "tgv") for p in (8, 10)])   # 3072 tets, high degree
 
 
 def _time_flushed(torch, stream, fn, reps, flush):
