@@ -828,6 +828,31 @@ esd_status esd_autotune_kernels(esd_mesh m, const double* u, int kernels, void* 
       }
     }
   }
+  // projection adjoint (esd_rhs_vjp): elements per CTA x threads, with the residual
+  // adjoint's current shape
+  if (kernels & ESD_TUNE_ADJOINT) {
+    float tbest = 1e30f;
+    const int emax = std::max(1, (int)(budget / smem_project(r, 1)));
+    for (int e = emax; e >= 1; e = e > 1 ? e / 2 : 0) {
+      for (int thr : {128, 256, 512}) {
+        LaunchCfg L = best;
+        L.eq = e;
+        L.tq = thr;
+        L.sq = smem_project(r, e);
+        float t = time_launches([&] {
+          return launch_vjp(m->R, m->M, L, u, m->ws_adj[0], m->ws_adj[1], m->ws_qbar, m->ws_qext, s);
+        }, s, 2);
+        if (verbose) std::fprintf(stderr, "esd_autotune: vjp-proj elems/CTA %3d threads %4d  %.4f ms\n", e, thr, t);
+        if (t < tbest) {
+          tbest = t;
+          best.eq = L.eq;
+          best.tq = L.tq;
+          best.sq = L.sq;
+        }
+      }
+      if (e == 1) break;
+    }
+  }
   // residual adjoint (esd_rhs_vjp): elements per CTA
   if (kernels & ESD_TUNE_ADJOINT) {
     float tbest = 1e30f;

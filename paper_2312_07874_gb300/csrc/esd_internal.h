@@ -105,6 +105,7 @@ struct LaunchCfg {
   int ea = 1, ta = 128;  size_t sa = 0;   // projection kernel: elements/CTA, threads, smem bytes
   int eb = 1, tb = 128;  size_t sb = 0;   // residual kernel
   int ev = 1, tv = 128;  size_t sv = 0;   // residual adjoint kernel
+  int eq = 1, tq = 128;  size_t sq = 0;   // projection adjoint kernel (projection-sized tiles)
 };
 
 // RK epilogue of the residual kernel: acc_out = acc_in + cb*k, stage_out = u0 + ca*k.

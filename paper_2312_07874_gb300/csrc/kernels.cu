@@ -512,6 +512,9 @@ LaunchCfg choose_launch(const RefTables& r) {
   L.ea = ea;
   L.ta = 256;
   L.sa = smem_project(r, ea);
+  L.eq = L.ea;
+  L.tq = L.ta;
+  L.sq = L.sa;
   // residual: E*T threads for the pair phases.  The kernels use up to ~255 registers, so an SM
   // holds at most 256 of their threads; pick E to maximise the threads doing pair work per SM
   // (CTAs per SM x E*T, limited by shared memory and registers), then lane utilisation.
@@ -635,11 +638,11 @@ cudaError_t launch_vjp(const DevRef& R, const DevMesh& M, const LaunchCfg& L, co
   else
     residual_adjoint_kernel<3><<<gb, L.tv, L.sv, s>>>(R, M, L.ev, cot, qbar, qext);
   if ((e = cudaGetLastError())) return e;
-  const unsigned ga = (unsigned)((M.E + L.ea - 1) / L.ea);
+  const unsigned ga = (unsigned)((M.E + L.eq - 1) / L.eq);
   if (R.dim == 2)
-    project_adjoint_kernel<2><<<ga, L.ta, L.sa, s>>>(R, M, L.ea, u, qbar, qext, grad);
+    project_adjoint_kernel<2><<<ga, L.tq, L.sq, s>>>(R, M, L.eq, u, qbar, qext, grad);
   else
-    project_adjoint_kernel<3><<<ga, L.ta, L.sa, s>>>(R, M, L.ea, u, qbar, qext, grad);
+    project_adjoint_kernel<3><<<ga, L.tq, L.sq, s>>>(R, M, L.eq, u, qbar, qext, grad);
   return cudaGetLastError();
 }
 
