@@ -39,8 +39,12 @@ class RK4Rollout(torch.autograd.Function):
         u = u0.detach().clone().contiguous()
         if checkpoint == "stages":
             ck = torch.empty((n_steps, 4) + tuple(u.shape), dtype=u.dtype, device=u.device)
+            # the step writes its stage inputs to one fixed buffer (so that its captured
+            # CUDA graph is reused by every step) and they are copied into the checkpoint
+            stage = torch.empty((4,) + tuple(u.shape), dtype=u.dtype, device=u.device)
             for s in range(n_steps):
-                esd_rk_step(mesh.handle, u, dt, ck[s])
+                esd_rk_step(mesh.handle, u, dt, stage)
+                ck[s].copy_(stage)
         elif checkpoint == "steps":
             ck = torch.empty((n_steps,) + tuple(u.shape), dtype=u.dtype, device=u.device)
             for s in range(n_steps):
