@@ -239,6 +239,12 @@ esd_status esd_debug_host_setup(const esd_mesh_desc* desc, double* wj, double* b
  * table-driven device implementations; x, y device arrays of n doubles. */
 esd_status esd_debug_math(int which, const double* x, double* y, int64_t n, void* stream);
 
+/* Host-side audit (no device needed): for every supported (dim, p), the shared-memory
+ * layouts of the residual and adjoint kernels are in bounds and disjoint where live
+ * together, bulk copies are 16-byte sized and aligned, and the default launch shapes fit
+ * one CTA.  ESD_OK, or ESD_ERR_UNSUPPORTED with the first violation in esd_last_error(). */
+esd_status esd_debug_check_layouts(void);
+
 /* Test hook for the failure path of the bounded waits (not in the paper): launches one
  * block that waits on a shared-memory barrier that nothing completes; after `seconds`
  * (0 < seconds <= 10) the wait gives up and sets the mesh's error flag, so that the next

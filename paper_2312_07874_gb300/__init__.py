@@ -69,6 +69,7 @@ SYMBOLS = {
     "esd_ref_info": ([ctypes.c_int, ctypes.c_int, ctypes.POINTER(esd_info)], ctypes.c_int),
     "esd_debug_host_setup": ([ctypes.POINTER(esd_mesh_desc)] + [ctypes.c_void_p] * 8, ctypes.c_int),
     "esd_debug_staging_timeout": ([ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p], ctypes.c_int),
+    "esd_debug_check_layouts": ([], ctypes.c_int),
     "esd_debug_math": ([ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p],
                        ctypes.c_int),
     "esd_status_string": ([ctypes.c_int], ctypes.c_char_p),
@@ -228,6 +229,11 @@ def esd_autotune_kernels(h, u, kernels, stream=None):
 def esd_launch_stage(h, stage, u=None, out=None, stream=None):
     _check(lib().esd_launch_stage(h, int(stage), _ptr(u) if u is not None else None,
                                   _ptr(out) if out is not None else None, _stream(stream)))
+
+
+def esd_debug_check_layouts():
+    """Host-side audit of the kernels' shared-memory layouts for every supported degree."""
+    _check(lib().esd_debug_check_layouts())
 
 
 def esd_debug_staging_timeout(handle, seconds=0.05, stream=None):

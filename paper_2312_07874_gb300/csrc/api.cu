@@ -936,6 +936,12 @@ esd_status esd_debug_host_setup(const esd_mesh_desc* d, double* wj, double* bj, 
   return ESD_OK;
 }
 
+esd_status esd_debug_check_layouts(void) {
+  std::string err;
+  if (!audit_layouts(&err)) return fail(ESD_ERR_UNSUPPORTED, err.c_str());
+  return ESD_OK;
+}
+
 esd_status esd_debug_math(int which, const double* x, double* y, int64_t n, void* stream) {
   if (which != 0 && which != 1) return fail(ESD_ERR_ARG, "which must be 0 (log) or 1 (exp)");
   esd_status st;

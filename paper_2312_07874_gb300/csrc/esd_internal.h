@@ -134,6 +134,7 @@ struct BatchItem {
 };
 
 LaunchCfg choose_launch(const RefTables& r);
+bool audit_layouts(std::string* err);   // kernels.cu, host only
 size_t smem_project(const RefTables& r, int e);
 size_t smem_residual(const RefTables& r, int e);
 size_t smem_residual_adj(const RefTables& r, int e);

@@ -17,6 +17,7 @@
 #include <cmath>
 #include <cstdio>
 #include <algorithm>
+#include <string>
 
 #include "adjoint.cuh"
 
@@ -557,6 +558,50 @@ LaunchCfg choose_launch(const RefTables& r) {
   L.tv = std::max(64, ((best * r.T + 31) / 32) * 32);
   L.sv = smem_residual_adj(r, best);
   return L;
+}
+
+// Host-side audit of the shared-memory layouts and default launch shapes of every
+// supported (dim, p): regions in bounds and disjoint where they are live together, bulk
+// copies 16-byte sized and aligned, footprints within one CTA.  No device involved.
+bool audit_layouts(std::string* err) {
+  char msg[256];
+  auto bad = [&](int dim, int p, const char* what) {
+    std::snprintf(msg, sizeof msg, "layout audit failed: dim %d p %d: %s", dim, p, what);
+    *err = msg;
+    return false;
+  };
+  for (int dim = 2; dim <= 3; ++dim) {
+    const int pmax = dim == 2 ? kMaxPTri : kMaxPTet;
+    for (int p = 1; p <= pmax; ++p) {
+      RefTables r;
+      std::string e2;
+      if (build_ref(dim, p, &r, &e2) != ESD_OK) return bad(dim, p, "reference tables");
+      const int NC = dim + 2, NF = dim + 5, NQ = dim + 2;
+      // residual kernel
+      const ResLayout L = dim == 2 ? res_layout<2>(r.Nq, r.Nfn, r.Np, r.n) : res_layout<3>(r.Nq, r.Nfn, r.Np, r.n);
+      if (L.pe % 2) return bad(dim, p, "residual element stride not 16-byte aligned");
+      if ((NF * r.Ntot * 8) % 16) return bad(dim, p, "state block not a multiple of 16 bytes");
+      if (L.oS + NF * r.Ntot > L.oR) return bad(dim, p, "states overlap the accumulators");
+      if (L.oMod + NC * r.Np > L.oR || L.oS2 + NC * r.Nq > L.oMod) return bad(dim, p, "transform scratch");
+      if (L.oR + NC * r.Nq > L.oH4 || L.oH4 + (dim == 3 ? NC * r.Nqf : 0) > L.pe) return bad(dim, p, "r / h4");
+      const LaunchCfg C = choose_launch(r);
+      if (smem_residual(r, C.eb) > kSmemBudget || smem_project(r, C.ea) > kSmemBudget)
+        return bad(dim, p, "default shape exceeds the shared-memory budget");
+      if (C.tb < C.eb * r.T || C.tb > 1024 || C.tb % 32) return bad(dim, p, "residual threads");
+      // residual adjoint
+      const AdjLayout A = dim == 2 ? adj_layout<2>(r.Nq, r.Nfn, r.Np, r.n) : adj_layout<3>(r.Nq, r.Nfn, r.Np, r.n);
+      if ((size_t)A.pe * 8 > kSmemBudget) return bad(dim, p, "adjoint footprint");
+      const int states_end = A.oSf + NF * r.Nfn;
+      if (states_end > A.oRb || (A.oIp >= 0 && A.oIp < states_end) ||
+          (A.oIp >= 0 && A.oIp + r.Nq + r.Nfn > A.oRb) || A.oM + NC * r.Np > A.oRb)
+        return bad(dim, p, "adjoint states / scratch");
+      if (A.oHb + NC * r.Nfn > (A.glob ? A.oPart : A.oQv)) return bad(dim, p, "adjoint h_b");
+      if (!A.glob && (A.oQf + NQ * r.Nfn > A.oPart)) return bad(dim, p, "adjoint q_b");
+      if (A.oPart + (dim == 3 ? NQ * r.T * A.ncol : 0) > A.pe) return bad(dim, p, "adjoint partials");
+      if (C.tv > 512 || C.tv < C.ev * r.T) return bad(dim, p, "adjoint threads");
+    }
+  }
+  return true;
 }
 
 cudaError_t set_smem_limits(const LaunchCfg& L, int dim) {

@@ -227,3 +227,10 @@ def test_empty_mesh_rejected():
     with pytest.raises(E.EsdError) as ex:
         E.esd_debug_host_setup(2, 2, np.zeros((0, 6, 2)), np.zeros((0, 3), np.int32), np.zeros((0, 3), np.int8))
     assert ex.value.status == -1
+
+
+def test_kernel_layouts_audited_for_every_degree():
+    """Shared-memory layouts, bulk-copy sizes and default launch shapes of every supported
+    (dim, p), checked on the host before any kernel runs (esd_debug_check_layouts)."""
+    import paper_2312_07874_gb300 as E
+    E.esd_debug_check_layouts()
