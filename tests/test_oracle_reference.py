@@ -179,3 +179,59 @@ def test_collapse_maps_vertices():
     assert np.all(img.sum(1) <= -1 + 1e-14)
     verts = {tuple(v) for v in np.round(img, 12)}
     assert verts == {(-1, -1, -1), (1, -1, -1), (-1, 1, -1), (-1, -1, 1)}
+
+
+def _lg_sbp_1d(q):
+    """The 1D Legendre-Gauss SBP operator Q1 = diag(w) D1 (Section 2.4) built from numpy's
+    Legendre routines alone: D1 = V' V^{-1} with the Legendre Vandermonde V on the nodes."""
+    leg = np.polynomial.legendre
+    x, w = leg.leggauss(q + 1)
+    V = leg.legvander(x, q)
+    dV = np.stack([leg.legval(x, leg.legder(np.eye(q + 1)[k])) for k in range(q + 1)], axis=1)
+    D1 = dV @ np.linalg.inv(V)
+    tL = leg.legvander(np.array([-1.0]), q)[0] @ np.linalg.inv(V)   # extrapolation to -1
+    tR = leg.legvander(np.array([1.0]), q)[0] @ np.linalg.inv(V)    # extrapolation to +1
+    return x, w, np.diag(w) @ D1, tL, tR
+
+
+def test_q1_eta1_line_operator_by_hand():
+    """q = 1 by hand: LG nodes -+1/sqrt(3), weights 1, linear Lagrange derivatives -+sqrt(3)/2,
+    so the 1D operator is (sqrt(3)/2)[[-1, 1], [-1, 1]] and Q1 + Q1^T = diag(-sqrt(3), sqrt(3)).
+    On the triangle (Eq. (tri_quadrature), Eq. (d1_2d)) the factor (1 - eta_2)/2 of the weight
+    cancels 2/(1 - eta_2) of D^(1), so each eta_1 line of Q^(1) = W D^(1) is w_2 Q1 = Q1."""
+    s = np.sqrt(3.0) / 2
+    Q1 = s * np.array([[-1.0, 1.0], [-1.0, 1.0]])
+    assert np.allclose(Q1 + Q1.T, np.diag([-np.sqrt(3.0), np.sqrt(3.0)]), atol=1e-15)
+    r = ref(2, 1)
+    for a2 in range(2):
+        line = [a1 * 2 + a2 for a1 in range(2)]   # alpha_1 slowest
+        assert np.abs(r.Q[0][np.ix_(line, line)] - Q1).max() < 1e-14
+    off = [(i, j) for i in range(4) for j in range(4) if (i % 2) != (j % 2)]
+    assert all(r.Q[0][i, j] == 0.0 for i, j in off)
+
+
+@pytest.mark.parametrize("dim,q", [(2, q) for q in (2, 3, 5, 8)] + [(3, q) for q in (2, 3, 4)])
+def test_eta1_lines_are_scaled_1d_lg_sbp(dim, q):
+    """The eta_1 lines of Q^(1) are scaled copies of the 1D LG SBP operator: on the triangle the
+    weight factor (1 - eta_2)/2 cancels 2/(1 - eta_2) of Eq. (d1_2d), leaving w_2(alpha_2) Q1;
+    on the tetrahedron (1 - eta_2)(1 - eta_3)/8 against 4/((1 - eta_2)(1 - eta_3)) of Eq. (d_3d)
+    leaves w_2(alpha_2) w_3(alpha_3)/2 Q1, with w_3 the Gauss-Jacobi(1,0) weights.  Q1 itself
+    satisfies Q1 + Q1^T = tR tR^T - tL tL^T (the 1D SBP property)."""
+    from scipy.special import roots_jacobi
+    x, w, Q1, tL, tR = _lg_sbp_1d(q)
+    assert np.abs(Q1 + Q1.T - (np.outer(tR, tR) - np.outer(tL, tL))).max() < 1e-12
+    r = ref(dim, q) if (dim, q) in CASES else RefElement(dim, q)
+    n = q + 1
+    Q = r.Q[0]
+    scale = np.abs(Q1).max()
+    if dim == 2:
+        lines = [((a2,), w[a2]) for a2 in range(n)]
+    else:
+        _, w3 = roots_jacobi(n, 1.0, 0.0)
+        lines = [((a2, a3), w[a2] * w3[a3] / 2) for a2 in range(n) for a3 in range(n)]
+    seen = np.zeros_like(Q, dtype=bool)
+    for rest, c in lines:
+        idx = [int(np.ravel_multi_index((a1,) + rest, (n,) * dim)) for a1 in range(n)]
+        assert np.abs(Q[np.ix_(idx, idx)] - c * Q1).max() < 1e-12 * scale
+        seen[np.ix_(idx, idx)] = True
+    assert np.all(Q[~seen] == 0.0)
