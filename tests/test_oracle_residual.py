@@ -160,3 +160,28 @@ def test_rk4_fourth_order():
         errs.append(abs(u - np.exp(lam)))
     rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
     assert np.all(rates > 3.8)
+
+
+@pytest.mark.parametrize("dim,p", [(2, 2), (2, 4), (3, 2), (3, 3)])
+def test_weight_adjusted_inverse_exact_on_polynomials(dim, p):
+    """Eq. (weight_adjusted_inverse): M~^-1 = V^T W J^-1 V inverts M_J = V^T W J V exactly on
+    modes c whenever J (V c) is a polynomial of degree <= p (the quadrature is exact to degree
+    2q), and only approximately otherwise.  J is planted as a positive affine function of xi."""
+    import copy
+    from oracle.pkd import modal_indices
+    D, _ = disc(dim, 3, p, True, "LF", "vortex" if dim == 2 else "tgv")
+    Dp = copy.copy(D)
+    Dp.geo = copy.copy(D.geo)
+    xi = D.ref.xi
+    J = 2.0 + xi @ np.array([0.3, -0.2, 0.1][:dim])
+    Dp.geo.J_vol = np.broadcast_to(J, (D.E, D.ref.Nq))
+    deg = np.array([sum(a) for a in modal_indices(dim, p)])
+    rng = np.random.default_rng(11)
+    c = rng.standard_normal((1, D.Np, D.Nc))
+    low = np.where(deg <= p - 1, 1.0, 0.0)[None, :, None] * c
+    MJ = lambda y: np.einsum("qi,q,qk,ekc->eic", D.V, D.ref.w * J, D.V, y)
+    assert np.abs(Dp.minv(MJ(low), np.arange(1)) - low).max() < 1e-13 * np.abs(low).max()
+    assert np.abs(Dp.minv(MJ(c), np.arange(1)) - c).max() > 1e-6 * np.abs(c).max()
+    # constant J: the weight-adjusted inverse is exactly M_J^-1 = I / J on every mode
+    Dp.geo.J_vol = np.full((D.E, D.ref.Nq), 1.7)
+    assert np.abs(Dp.minv(1.7 * c, np.arange(1)) - c).max() < 1e-13 * np.abs(c).max()
