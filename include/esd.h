@@ -160,7 +160,8 @@ esd_status esd_rhs_vjp(esd_mesh mesh, const double* u, const double* cot, double
 /* One classical RK4 step of size dt in place on u (not in the paper, which uses DP8).
  * stage_ckpt: NULL or device [4][n_elem][N_c][N_p*]; when given, the four stage
  * inputs are stored there for esd_rk_step_vjp.  The launch sequence is captured in a
- * CUDA graph per (u, dt, stage_ckpt, stream) and replayed on later calls. */
+ * CUDA graph per (u, dt, stage_ckpt, stream) and replayed on later calls; the 16 most
+ * recently captured graphs are kept per mesh. */
 esd_status esd_rk_step(esd_mesh mesh, double* u, double dt, double* stage_ckpt, void* stream);
 
 /* Discrete adjoint of one esd_rk_step: given the stage checkpoints written by the forward
@@ -190,7 +191,11 @@ esd_status esd_batch_create(const esd_mesh* meshes, int n, esd_batch* out);
 esd_status esd_batch_destroy(esd_batch batch);
 /* u[i], dudt[i]: device state arrays of mesh i (layouts as above). */
 esd_status esd_batch_rhs(esd_batch batch, const double* const* u, double* const* dudt, void* stream);
-/* One RK4 step of every mesh; dt[i] is a HOST array of step sizes. */
+/* One RK4 step of every mesh; dt[i] is a HOST array of step sizes.  Both batch calls
+ * capture their launches in a CUDA graph per (pointers, step sizes, stream), replayed on
+ * later calls with the same arguments; the 16 most recent are kept per batch (dropping
+ * one waits for the device).  An RK4 step uses each member mesh's workspace, so two
+ * batches (or a batch and a direct call) sharing a mesh must not overlap on the GPU. */
 esd_status esd_batch_rk_step(esd_batch batch, double* const* u, const double* dt, void* stream);
 
 /* Autotuner (not in the paper): time the projection kernel over elements-per-CTA x

@@ -42,6 +42,9 @@ esd_status check_dev(const void* p, const char* name) {
 }
 }  // namespace
 
+// Captured RK4 (and batch) graphs kept per handle; the oldest is dropped beyond this.
+constexpr size_t kMaxCachedGraphs = 16;
+
 struct GraphEntry {
   double* u;
   double dt;
@@ -344,14 +347,16 @@ esd_status esd_rk_step(esd_mesh m, double* u, double dt, double* ck, void* strea
   if (e) return cuda_fail(e, "begin capture");
   cudaError_t e1 = rk_sequence(m, u, dt, ck, s);
   e = cudaStreamEndCapture(s, &graph);
-  if (e1) return cuda_fail(e1, "rk capture");
-  if (e) return cuda_fail(e, "end capture");
+  if (e1 || e) {
+    if (!e) cudaGraphDestroy(graph);
+    return e1 ? cuda_fail(e1, "rk capture") : cuda_fail(e, "end capture");
+  }
   cudaGraphExec_t exec;
   e = cudaGraphInstantiate(&exec, graph, 0);
   cudaGraphDestroy(graph);
   if (e) return cuda_fail(e, "graph instantiate");
-  if (m->graphs.size() >= 16) {
-    cudaGraphExecDestroy(m->graphs.front().exec);
+  if (m->graphs.size() >= kMaxCachedGraphs) {
+    cudaGraphExecDestroy(m->graphs.front().exec);   // an in-flight launch completes first
     m->graphs.erase(m->graphs.begin());
   }
   m->graphs.push_back({u, dt, ck, s, exec});
@@ -439,7 +444,14 @@ struct BatchGraph {
   cudaStream_t s;
   int kind;   // 0: rhs, 1: rk step
   std::vector<BatchMesh*> d_tables;   // device BatchMesh arrays used by the graph (one per launch)
-  cudaGraphExec_t exec;
+  cudaGraphExec_t exec = nullptr;
+  // callers make sure no launch of the graph is still in flight
+  void release() {
+    if (exec) cudaGraphExecDestroy(exec);
+    exec = nullptr;
+    for (auto* p : d_tables) cudaFree(p);
+    d_tables.clear();
+  }
 };
 
 struct esd_batch_s {
@@ -448,7 +460,7 @@ struct esd_batch_s {
   std::vector<BatchGraph> graphs;
   std::vector<void*> allocs;
   ~esd_batch_s() {
-    for (auto& g : graphs) cudaGraphExecDestroy(g.exec);
+    for (auto& g : graphs) g.release();
     for (void* p : allocs) cudaFree(p);
   }
 };
@@ -582,8 +594,10 @@ static esd_status batch_run(esd_batch b, int kind, const std::vector<const doubl
   G.s = s;
   G.kind = kind;
   cudaError_t e = batch_sequence(b, G, s);  // per-launch device tables (allocated outside capture)
-  if (e) return cuda_fail(e, "batch tables");
-  for (auto* p : G.d_tables) b->allocs.push_back(p);
+  if (e) {
+    G.release();
+    return cuda_fail(e, "batch tables");
+  }
   cudaStream_t cs = s;
   cudaStream_t own = nullptr;
   if (cs == nullptr) {  // the legacy stream cannot be captured: capture on a private stream
@@ -608,11 +622,13 @@ static esd_status batch_run(esd_batch b, int kind, const std::vector<const doubl
   };
   if (e1) {
     release();
+    G.release();
     return cuda_fail(e1, "batch streams");
   }
   cudaGraph_t graph;
   if ((e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal))) {
     release();
+    G.release();
     return cuda_fail(e, "batch capture");
   }
   const int nst = kind == 0 ? 1 : 4;
@@ -635,12 +651,22 @@ static esd_status batch_run(esd_batch b, int kind, const std::vector<const doubl
   if (e1 || e) {
     if (!e) cudaGraphDestroy(graph);
     release();
+    G.release();
     return e1 ? cuda_fail(e1, "batch launch") : cuda_fail(e, "batch end capture");
   }
   e = cudaGraphInstantiate(&G.exec, graph, 0);
   cudaGraphDestroy(graph);
   release();
-  if (e) return cuda_fail(e, "batch graph instantiate");
+  if (e) {
+    G.exec = nullptr;
+    G.release();
+    return cuda_fail(e, "batch graph instantiate");
+  }
+  if (b->graphs.size() >= kMaxCachedGraphs) {
+    cudaDeviceSynchronize();   // the evicted graph's launches still read its device tables
+    b->graphs.front().release();
+    b->graphs.erase(b->graphs.begin());
+  }
   b->graphs.push_back(G);
   e = cudaGraphLaunch(G.exec, s);
   return e ? cuda_fail(e, "batch graph launch") : ESD_OK;

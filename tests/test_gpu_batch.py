@@ -92,3 +92,40 @@ def test_autotune_keeps_results_and_valid_shapes():
         after = m.rhs(u)
         torch.cuda.synchronize()
         assert torch.equal(before, after)
+
+
+def test_graph_caches_evict_and_recapture():
+    """More argument sets than the 16 cached graphs: every call still gives the per-mesh
+    result, including a set whose graph was dropped and is captured again."""
+    import torch
+    import paper_2312_07874_gb300 as E
+    ms = _meshes()[:3]
+    b = E.esd_batch_create([m.handle for m, _ in ms])
+    refs = [m.rhs(u) for m, u in ms]
+    first = None
+    for k in range(18):
+        outs = [torch.empty_like(u) for _, u in ms]
+        E.esd_batch_rhs(b, [u for _, u in ms], outs)
+        torch.cuda.synchronize()
+        assert all(torch.equal(o, r) for o, r in zip(outs, refs))
+        first = first or outs
+    for o in first:
+        o.zero_()
+    E.esd_batch_rhs(b, [u for _, u in ms], first)
+    torch.cuda.synchronize()
+    assert all(torch.equal(o, r) for o, r in zip(first, refs))
+    E.esd_batch_destroy(b)
+    # per-mesh RK4 graphs: 18 step sizes on a side stream against direct launches on the
+    # legacy stream (no graph)
+    m, u0 = ms[0]
+    s = torch.cuda.Stream()
+    for k in range(18):
+        dt = 1e-3 * (1 + 0.05 * k)
+        a, c = u0.clone(), u0.clone()
+        torch.cuda.synchronize()
+        with torch.cuda.stream(s):
+            m.rk_step(a, dt)
+        s.synchronize()
+        m.rk_step(c, dt)
+        torch.cuda.synchronize()
+        assert torch.equal(a, c)
