@@ -345,12 +345,46 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def _kernel_hash():
+KERNEL_SOURCES = ("device.cuh", "residual_inst.cuh", "residual_d3.cu", "esd_internal.h")
+
+
+def _code_tokens(src):
+    """C/C++ source without comments, with blank lines, indentation and runs of blanks
+    collapsed: a comment or layout edit leaves it unchanged, a code edit changes it."""
+    import re
+    out, i, n = [], 0, len(src)
+    while i < n:
+        c = src[i]
+        if src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+            out.append(" ")
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            j = n if j < 0 else j + 2
+            out.append("\n" if "\n" in src[i:j] else " ")
+            i = j
+        elif c in "\"'":
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        else:
+            out.append(c)
+            i += 1
+    code = re.sub(r"[ \t]+", " ", "".join(out))
+    return re.sub(r" ?\n\s*", "\n", code).strip()
+
+
+def _kernel_hash(read=None):
+    """Hash of the code (comments and layout excluded) of residual_kernel<3, N>'s sources;
+    the adjoint and projection kernels live elsewhere.  `read(name)` returns a file's text."""
     import hashlib
+    read = read or (lambda f: open(os.path.join(ROOT, "paper_2312_07874_gb300", "csrc", f)).read())
     h = hashlib.sha256()
-    # sources of residual_kernel<3, N> (the adjoint and projection kernels live elsewhere)
-    for f in ("device.cuh", "residual_inst.cuh", "residual_d3.cu", "esd_internal.h"):
-        h.update(open(os.path.join(ROOT, "paper_2312_07874_gb300", "csrc", f), "rb").read())
+    for f in KERNEL_SOURCES:
+        h.update(_code_tokens(read(f)).encode())
     return h.hexdigest()
 
 

@@ -35,7 +35,8 @@ __device__ __forceinline__ NodeState<D> load_state(const double* S, int stride, 
 
 // ---------------------------------------------------------------------------
 // The directional entropy-conservative flux f#(U^-, U^+, n) = sum_m n_m f_m^#
-// (Eq. (ranocha_flux), reading R4: the energy component is
+// (Eq. (ranocha_flux); the printed one-half is read as multiplying v^-.v^+ alone, since
+// the printed placement would make the flux inconsistent, so the energy component is
 // rho_ln {{v}}.n (v^-.v^+/2 + 1/((gamma-1) {{rho/p}}_ln)) + (p^- v^+.n + p^+ v^-.n)/2),
 // evaluated FP64-lean for the pair loops:
 //

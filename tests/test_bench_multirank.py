@@ -48,3 +48,18 @@ def test_reference_arm_under_torchrun():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["value"] > 0 and d["n_gpus"] == 2
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_kernel_hash_ignores_comments_not_code():
+    """The traffic record is tied to the residual kernel's code: comment and layout edits
+    keep the hash, code edits change it."""
+    import bench
+    src = {f: open(os.path.join(ROOT, "paper_2312_07874_gb300", "csrc", f)).read() for f in bench.KERNEL_SOURCES}
+    base = bench._kernel_hash(lambda f: src[f])
+    commented = dict(src)
+    commented["device.cuh"] = "// a new comment\n" + src["device.cuh"].replace("\n", "  \n", 3) + "\n/* end\n */\n"
+    assert bench._kernel_hash(lambda f: commented[f]) == base
+    edited = dict(src)
+    edited["device.cuh"] = src["device.cuh"].replace("0.5", "0.25", 1)
+    assert edited["device.cuh"] != src["device.cuh"]
+    assert bench._kernel_hash(lambda f: edited[f]) != base

@@ -170,8 +170,9 @@ def test_pkd_spans_total_degree_space(dim, p):
 
 
 def test_collapse_maps_vertices():
-    """chi maps the square/cube onto the reference simplex; the tetrahedron map as read (G1)
-    sends cube vertices to simplex vertices and the Jacobian determinant matches the weights."""
+    """chi maps the square/cube onto the reference simplex; the tetrahedron map, read with
+    (1 - eta_3) as the third factor of xi_1 where the print repeats (1 - eta_2), sends cube
+    vertices to simplex vertices and the Jacobian determinant matches the weights."""
     tri = collapse(np.array([[-1, -1], [1, -1], [-1, 1], [1, 1]], float))
     assert np.allclose(tri, [[-1, -1], [1, -1], [-1, 1], [-1, 1]])
     cube = np.array(list(itertools.product([-1.0, 1.0], repeat=3)))
