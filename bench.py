@@ -281,7 +281,8 @@ def run_ours(args):
     if os.path.exists(tpath):
         tj = json.load(open(tpath))
         if tj.get("kernel_source_sha256") == _kernel_hash():
-            traffic = tj.get("dram_bytes_per_launch")
+            # captured on tetrahedra at p = 4; traffic grows in proportion to the elements
+            traffic = tj["dram_bytes_per_element"] * nE
     pflops = project_kernel_flops(D, p)
 
     # ---- end to end through the public API: pinned H2D, RK4 step, D2H ----
