@@ -63,3 +63,16 @@ def test_kernel_hash_ignores_comments_not_code():
     edited["device.cuh"] = src["device.cuh"].replace("0.5", "0.25", 1)
     assert edited["device.cuh"] != src["device.cuh"]
     assert bench._kernel_hash(lambda f: edited[f]) != base
+
+
+def test_cpu_baseline_all_cores_small_mesh(monkeypatch):
+    """The all-core oracle baseline forks one worker per core on distinct element blocks
+    (a 162-tetrahedron mesh here) and reports the cores it used."""
+    import bench
+    monkeypatch.setitem(bench.WORKLOAD, "M", 3)
+    monkeypatch.setattr(bench, "_ORACLE", {})
+    out = bench.cpu_baseline_all_cores(n_el=4)
+    cores = max(1, min(64, len(os.sched_getaffinity(0))))
+    assert out["cores"] == cores and out["kind"] == "oracle" and out["value"] > 0
+    assert out["unit"] == bench.UNIT
+    assert f"{cores} forked workers x {max(1, min(4, 162 // cores))} distinct elements" in out["sample"]
