@@ -48,6 +48,7 @@ def test_reference_arm_under_torchrun():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["value"] > 0 and d["n_gpus"] == 2
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
+    assert d["cpu_baseline"]["cores"] == max(1, min(64, len(os.sched_getaffinity(0))))
 
 
 def test_kernel_hash_ignores_comments_not_code():
