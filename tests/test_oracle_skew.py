@@ -1,0 +1,104 @@
+"""Pins for the oracle's conservative and skew-symmetric forms (Section 4.4, Eq. (rhs_cons),
+Eq. (rhs_skew)): they coincide on affine meshes; the skew-symmetric form preserves a
+uniform state and conserves on curved meshes, and for linear advection it conserves the
+discrete energy u^T r (central flux) or dissipates it (upwind) on curved meshes, which
+the conservative form does not."""
+from functools import lru_cache
+
+import numpy as np
+import pytest
+
+import esd_inputs as I
+from oracle import euler, skew
+from oracle.residual import Discretization
+
+
+@lru_cache(maxsize=None)
+def disc(dim, M, p, warp):
+    L = 2 * np.pi
+    mesh, X = I.config_mesh(dim, M, L, p, warp)
+    return Discretization(dim, p, X, mesh.nbr_elem, mesh.nbr_face)
+
+
+def euler_state(D, seed):
+    f = I.config_state_fn(D.dim, 2 * np.pi, "vortex" if D.dim == 2 else "tgv")
+    um = np.einsum("ij,i,eic->ecj", D.V, D.ref.w, f(D.geo.x_vol))
+    return um + I.seeded_normal(seed, um.shape, 1e-3)
+
+
+CASES = [(2, 3, 2), (2, 3, 4), (3, 3, 2)]
+
+
+@pytest.mark.parametrize("dim,M,p", CASES)
+def test_forms_coincide_on_affine_meshes(dim, M, p):
+    """With constant metrics G^(l,m) and J^zeta n = G^T nhat, the SBP property turns
+    Eq. (rhs_skew) into Eq. (rhs_cons) exactly; on curved meshes whose metric terms are
+    not affine functions of xi (sine-warped, p >= 3 triangles, p >= 2 tetrahedra with the
+    curl-form metrics) they differ."""
+    model = skew.EulerModel(dim)
+    D = disc(dim, M, p, False)
+    um = euler_state(D, 3)
+    el = np.arange(min(D.E, 12))
+    a = skew.nodal_residual(D, um, model, "skew", el)
+    b = skew.nodal_residual(D, um, model, "cons", el)
+    assert np.abs(a - b).max() < 1e-12 * np.abs(b).max()
+    if dim == 2 and p < 3:
+        return
+    Dc = disc(dim, M, p, True)
+    umc = euler_state(Dc, 3)
+    a = skew.nodal_residual(Dc, umc, model, "skew", el)
+    b = skew.nodal_residual(Dc, umc, model, "cons", el)
+    assert np.abs(a - b).max() > 1e-8 * np.abs(b).max()
+
+
+@pytest.mark.parametrize("dim,M,p", CASES)
+def test_skew_free_stream_on_curved_meshes(dim, M, p):
+    """A uniform state gives r = 0: Q 1 = 0, the discrete metric identities, and R exact
+    on the metric terms cancel the volume against the facet terms."""
+    D = disc(dim, M, p, True)
+    ubar = euler.conservative(np.array(1.3), np.array([0.4, -0.7, 0.2][:dim]), np.array(2.1))
+    un = np.broadcast_to(ubar, (D.E, D.ref.Nq, D.Nc))
+    um = np.einsum("ij,i,eic->ecj", D.V, D.ref.w, un)
+    r = skew.nodal_residual(D, um, skew.EulerModel(dim), "skew", np.arange(min(D.E, 20)))
+    assert np.abs(r).max() < 1e-12 * np.abs(ubar).max()
+
+
+@pytest.mark.parametrize("dim,M,p", CASES)
+def test_skew_conservation_on_curved_meshes(dim, M, p):
+    """sum_kappa 1^T r = -sum_kappa sum_zeta 1^T B J^zeta f* = 0 on a periodic mesh, and the
+    same for sum_kappa 1^T W J V d u~/dt through the weight-adjusted inverse."""
+    D = disc(dim, M, p, True)
+    model = skew.EulerModel(dim)
+    um = euler_state(D, 5)
+    r = skew.nodal_residual(D, um, model, "skew")
+    scale = np.abs(r).sum(axis=(0, 1))
+    assert np.all(np.abs(r.sum(axis=(0, 1))) < 1e-13 * scale)
+    dudt = skew.rhs(D, um, model, "skew")
+    rate = D.conservation_rate(dudt)
+    y = np.einsum("ij,ecj->eic", D.V, dudt)
+    scale = np.einsum("i,ei,eic->c", D.ref.w, D.geo.J_vol, np.abs(y))
+    assert np.all(np.abs(rate) < 1e-13 * scale)
+
+
+@pytest.mark.parametrize("dim,M,p", CASES + [(3, 3, 3)])
+def test_skew_energy_for_linear_advection_on_curved_meshes(dim, M, p):
+    """f_m = a_m u: the skew-symmetric volume terms cancel in u^T r for any metric terms, so
+    with the central interface flux sum_kappa u^T r = 0 (d/dt of the weight-adjusted energy
+    u~^T M~ u~ / 2) and with upwinding it is negative.  The conservative form has no such
+    identity once the metric terms are of higher degree (checked at p >= 3 here)."""
+    D = disc(dim, M, p, True)
+    a = np.array([1.0, 0.5, -0.3][:dim])
+    um = I.seeded_normal(9, (D.E, 1, D.Np), 1.0)
+    u, _ = skew.nodal_states(D, um)
+
+    def energy_rate(model, form):
+        r = skew.nodal_residual(D, um, model, form)
+        return float(np.sum(u * r)), float(np.sum(np.abs(u * r)))
+
+    ent, scale = energy_rate(skew.AdvectionModel(a), "skew")
+    assert abs(ent) < 1e-13 * scale
+    ent_up, scale_up = energy_rate(skew.AdvectionModel(a, upwind=True), "skew")
+    assert ent_up < -1e-3 * scale_up
+    if p >= 3:
+        ent_cons, scale_cons = energy_rate(skew.AdvectionModel(a), "cons")
+        assert abs(ent_cons) > 1e-8 * scale_cons
