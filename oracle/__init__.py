@@ -14,6 +14,8 @@ Modules
   euler      Section 7.1-2 Euler flux, entropy variables, log mean, Ranocha flux, Davis speed
   residual   Section 4.4-6, 5, 6   dense, sparse and hybridized residual routes; projection;
                            weight-adjusted inverse; diagnostics
+  skew       Section 4.4   conservative and skew-symmetric nodal forms (Eq. (rhs_cons),
+                           Eq. (rhs_skew)) for Euler and scalar linear advection
   timestep   classical RK4 (not in the paper)
   jacobian   complex-step Jacobian-vector products (not in the paper)
 
