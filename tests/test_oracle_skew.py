@@ -102,3 +102,28 @@ def test_skew_energy_for_linear_advection_on_curved_meshes(dim, M, p):
     if p >= 3:
         ent_cons, scale_cons = energy_rate(skew.AdvectionModel(a), "cons")
         assert abs(ent_cons) > 1e-8 * scale_cons
+
+
+@pytest.mark.parametrize("dim,M,p", [(2, 3, 3), (3, 3, 2)])
+def test_skew_volume_term_is_a_line_pair_sum(dim, M, p):
+    """The volume term of Eq. (rhs_skew) equals sum_j sum_m c^m_ij f_m(u_j) with
+    c^m_ij = 1/2 sum_l (Q^(l)_ji G_lm(j) - G_lm(i) Q^(l)_ij), and c^m_ij vanishes unless i
+    and j lie on a common collapsed-coordinate line (the sparsity of Q^(l), Section 5.1)."""
+    D = disc(dim, M, p, True)
+    um = euler_state(D, 11)
+    model = skew.EulerModel(dim)
+    u, _ = skew.nodal_states(D, um)
+    e = 4
+    G = D.geo.G_vol[e]
+    f = [model.flux(u[e], m) for m in range(dim)]
+    vol = sum(0.5 * (D.ref.Q[l].T @ (G[:, l, m][:, None] * f[m]) - G[:, l, m][:, None] * (D.ref.Q[l] @ f[m]))
+              for l in range(dim) for m in range(dim))
+    alpha = D.ref.alpha
+    same_line = (alpha[:, None, :] == alpha[None, :, :]).sum(-1) >= dim - 1
+    pair = np.zeros_like(vol)
+    for m in range(dim):
+        c = sum(0.5 * (D.ref.Q[l].T * G[None, :, l, m] - G[:, l, m][:, None] * D.ref.Q[l]) for l in range(dim))
+        assert np.all(c[~same_line] == 0.0)
+        assert np.allclose(np.diag(c), 0.0, atol=1e-13 * np.abs(c).max())
+        pair += c @ f[m]
+    assert np.abs(pair - vol).max() < 1e-13 * np.abs(vol).max()
