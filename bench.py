@@ -342,7 +342,9 @@ def run_ours(args):
         "clocks": clk,
     }
     if rank == 0:
-        line["cpu_baseline"] = cpu_baseline(seconds=args.cpu_seconds) if args.cpu_seconds > 0 else None
+        # the host baselines are taken at N = 1 only (at N > 1 the other ranks would wait)
+        line["cpu_baseline"] = (cpu_baseline(seconds=args.cpu_seconds)
+                                if args.cpu_seconds > 0 and world == 1 else None)
         line["cpu_baseline_all_cores"] = all_cores
         print(json.dumps(line), flush=True)
     if world > 1:
