@@ -11,6 +11,24 @@
 
 #include "esd_internal.h"
 
+// NVTX ranges name each entry point's host-side span (enqueue, capture or graph launch) for
+// profilers (e.g. ncu --nvtx --nvtx-include "esd_rhs/").  Header-only NVTX 3: without an
+// attached tool the calls return at once.  Built without it if the header is absent.
+#if __has_include(<nvtx3/nvToolsExt.h>)
+#include <nvtx3/nvToolsExt.h>
+namespace {
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+}  // namespace
+#define ESD_RANGE(name) NvtxRange esd_nvtx_range_(name)
+#else
+#define ESD_RANGE(name) ((void)0)
+#endif
+
 using namespace esd;
 
 namespace {
@@ -120,6 +138,7 @@ const char* esd_status_string(esd_status s) {
 const char* esd_last_error(void) { return g_err.c_str(); }
 
 esd_status esd_mesh_create(const esd_mesh_desc* d, esd_mesh* out) {
+  ESD_RANGE("esd_mesh_create");
   if (!d || !out) return fail(ESD_ERR_ARG, "null descriptor or output");
   *out = nullptr;
   if (d->dim != 2 && d->dim != 3) return fail(ESD_ERR_ARG, "dim must be 2 or 3");
@@ -273,6 +292,7 @@ esd_status esd_mesh_volume_nodes(esd_mesh m, double* x) {
 }
 
 esd_status esd_l2_project(esd_mesh m, const double* un, double* um, void* stream) {
+  ESD_RANGE("esd_l2_project");
   if (!m) return fail(ESD_ERR_ARG, "null mesh");
   esd_status st;
   if ((st = check_dev(un, "u_nodal")) || (st = check_dev(um, "u_modal"))) return st;
@@ -281,6 +301,7 @@ esd_status esd_l2_project(esd_mesh m, const double* un, double* um, void* stream
 }
 
 esd_status esd_project_entropy(esd_mesh m, const double* u, double* w, void* stream) {
+  ESD_RANGE("esd_project_entropy");
   if (!m) return fail(ESD_ERR_ARG, "null mesh");
   esd_status st;
   if ((st = check_dev(u, "u")) || (st = check_dev(w, "w_modal"))) return st;
@@ -289,6 +310,7 @@ esd_status esd_project_entropy(esd_mesh m, const double* u, double* w, void* str
 }
 
 esd_status esd_rhs(esd_mesh m, const double* u, double* dudt, void* stream) {
+  ESD_RANGE("esd_rhs");
   if (!m) return fail(ESD_ERR_ARG, "null mesh");
   esd_status st;
   if ((st = check_dev(u, "u")) || (st = check_dev(dudt, "dudt"))) return st;
@@ -327,6 +349,7 @@ static cudaError_t rk_sequence(esd_mesh m, double* u, double dt, double* ck, cud
 }
 
 esd_status esd_rk_step(esd_mesh m, double* u, double dt, double* ck, void* stream) {
+  ESD_RANGE("esd_rk_step");
   if (!m) return fail(ESD_ERR_ARG, "null mesh");
   esd_status st;
   if ((st = check_dev(u, "u"))) return st;
@@ -365,6 +388,7 @@ esd_status esd_rk_step(esd_mesh m, double* u, double dt, double* ck, void* strea
 }
 
 esd_status esd_diagnostics(esd_mesh m, const double* u, double* out, void* stream) {
+  ESD_RANGE("esd_diagnostics");
   if (!m) return fail(ESD_ERR_ARG, "null mesh");
   esd_status st;
   if ((st = check_dev(u, "u")) || (st = check_dev(out, "out"))) return st;
@@ -380,6 +404,7 @@ esd_status esd_diagnostics(esd_mesh m, const double* u, double* out, void* strea
 }
 
 esd_status esd_integrals(esd_mesh m, const double* u, double* out, void* stream) {
+  ESD_RANGE("esd_integrals");
   if (!m) return fail(ESD_ERR_ARG, "null mesh");
   esd_status st;
   if ((st = check_dev(u, "u")) || (st = check_dev(out, "out"))) return st;
@@ -391,6 +416,7 @@ esd_status esd_integrals(esd_mesh m, const double* u, double* out, void* stream)
 }
 
 esd_status esd_rhs_vjp(esd_mesh m, const double* u, const double* cot, double* grad, void* stream) {
+  ESD_RANGE("esd_rhs_vjp");
   if (!m) return fail(ESD_ERR_ARG, "null mesh");
   esd_status st;
   if ((st = check_dev(u, "u")) || (st = check_dev(cot, "cot")) || (st = check_dev(grad, "grad"))) return st;
@@ -405,6 +431,7 @@ esd_status esd_rhs_vjp(esd_mesh m, const double* u, const double* cot, double* g
 //          k2_b = dt/3 c + dt/2 Y3_b;  Y2_b = J(Y2)^T k2_b;  k1_b = dt/6 c + dt/2 Y2_b;
 //          Y1_b = J(Y1)^T k1_b;  u_b = c + Y1_b + Y2_b + Y3_b + Y4_b.
 esd_status esd_rk_step_vjp(esd_mesh m, const double* ck, double dt, const double* co, double* ci, void* stream) {
+  ESD_RANGE("esd_rk_step_vjp");
   if (!m) return fail(ESD_ERR_ARG, "null mesh");
   esd_status st;
   if ((st = check_dev(ck, "stage_ckpt")) || (st = check_dev(co, "cot_out")) || (st = check_dev(ci, "cot_in")))
@@ -673,6 +700,7 @@ static esd_status batch_run(esd_batch b, int kind, const std::vector<const doubl
 }
 
 esd_status esd_batch_rhs(esd_batch b, const double* const* u, double* const* dudt, void* stream) {
+  ESD_RANGE("esd_batch_rhs");
   if (!b || !u || !dudt) return fail(ESD_ERR_ARG, "null argument");
   const size_t n = b->meshes.size();
   std::vector<const double*> ptrs(2 * n);
@@ -687,6 +715,7 @@ esd_status esd_batch_rhs(esd_batch b, const double* const* u, double* const* dud
 }
 
 esd_status esd_batch_rk_step(esd_batch b, double* const* u, const double* dt, void* stream) {
+  ESD_RANGE("esd_batch_rk_step");
   if (!b || !u || !dt) return fail(ESD_ERR_ARG, "null argument");
   const size_t n = b->meshes.size();
   std::vector<const double*> ptrs(n);
@@ -798,6 +827,7 @@ esd_status esd_autotune(esd_mesh m, const double* u, void* stream) {
 }
 
 esd_status esd_autotune_kernels(esd_mesh m, const double* u, int kernels, void* stream) {
+  ESD_RANGE("esd_autotune_kernels");
   if (!m) return fail(ESD_ERR_ARG, "null mesh");
   if (kernels & ~ESD_TUNE_ALL) return fail(ESD_ERR_ARG, "unknown kernel bits");
   esd_status st;
