@@ -15,7 +15,11 @@ Readings of the print:
   (Algorithms 2 and 3 there).  Written here from the identity
   ln(b/a) = 2 artanh(f), f = (b-a)/(b+a): with u = f^2,
   {{a}}_ln = (a+b) / (2 + 2u/3 + 2u^2/5 + 2u^3/7 + ...), used for u < 1e-4,
-  where the truncation is below 1e-17 relative; otherwise (b-a)/ln(b/a).
+  where the truncation after four terms is below 1.2e-17 relative (FP64; more terms
+  in extended precision); otherwise (b-a)/ln(b/a).
+
+Every function works in the floating-point type of its arguments (FP64, complex128
+for complex steps, or np.longdouble for the extended-precision evaluation).
 """
 import numpy as np
 
@@ -90,11 +94,26 @@ def cons_from_entropy(w, gamma=GAMMA):
     return conservative(rho, v, p, gamma)
 
 
+def _artanh_series(u):
+    """2 artanh(f)/f = 2 sum_k u^k/(2k+1), u = f^2, truncated for u < LOGMEAN_CUTOFF
+    where the first omitted term is below the unit roundoff of the working precision:
+    four terms in FP64 (truncation < 1.2e-17), more in extended precision."""
+    R = np.real(np.asarray(u)).dtype.type
+    eps = np.finfo(R).eps
+    K = 3
+    while LOGMEAN_CUTOFF ** (K + 1) / (2 * K + 3) > eps / 16:
+        K += 1
+    acc = R(2) / R(2 * K + 1)
+    for k in range(K - 1, -1, -1):
+        acc = R(2) / R(2 * k + 1) + u * acc
+    return acc
+
+
 def log_mean(a, b):
     """{{a}}_ln of Section 7.2 (series branch for nearly equal arguments)."""
     f = (b - a) / (b + a)
     u = f * f
-    series = (a + b) / (2.0 + u * (2.0 / 3.0 + u * (2.0 / 5.0 + u * (2.0 / 7.0))))
+    series = (a + b) / _artanh_series(u)
     safe_b = np.where(np.real(u) < LOGMEAN_CUTOFF, 2.0 * a + 1.0, b)   # avoid 0/0 in the unused branch
     direct = (safe_b - a) / np.log(safe_b / a)
     return np.where(np.real(u) < LOGMEAN_CUTOFF, series, direct)
@@ -104,7 +123,7 @@ def inv_log_mean(a, b):
     """1 / {{a}}_ln with the same branches."""
     f = (b - a) / (b + a)
     u = f * f
-    series = (2.0 + u * (2.0 / 3.0 + u * (2.0 / 5.0 + u * (2.0 / 7.0)))) / (a + b)
+    series = _artanh_series(u) / (a + b)
     safe_b = np.where(np.real(u) < LOGMEAN_CUTOFF, 2.0 * a + 1.0, b)
     direct = np.log(safe_b / a) / (safe_b - a)
     return np.where(np.real(u) < LOGMEAN_CUTOFF, series, direct)

@@ -26,19 +26,24 @@ Oracle (test infrastructure only).
 """
 import numpy as np
 
+from .jacobi import _working_type
 
-def lattice(dim, P):
+
+def lattice(dim, P, dtype=float):
+    """The equispaced degree-P lattice -1 + 2 i/P, first index fastest, in type ``dtype``."""
+    T = np.dtype(dtype).type
+    c = lambda i: T(-1) + T(2 * i) / T(P)
     pts = []
     if dim == 2:
         for j in range(P + 1):
             for i in range(P + 1 - j):
-                pts.append((-1 + 2.0 * i / P, -1 + 2.0 * j / P))
+                pts.append((c(i), c(j)))
     else:
         for k in range(P + 1):
             for j in range(P + 1 - k):
                 for i in range(P + 1 - j - k):
-                    pts.append((-1 + 2.0 * i / P, -1 + 2.0 * j / P, -1 + 2.0 * k / P))
-    return np.array(pts)
+                    pts.append((c(i), c(j), c(k)))
+    return np.array(pts, dtype=T)
 
 
 def _barycentric(xi):
@@ -47,7 +52,7 @@ def _barycentric(xi):
     xi = np.atleast_2d(xi)
     dim = xi.shape[1]
     lam = np.concatenate([1.0 - (xi + 1.0).sum(1, keepdims=True) / 2.0, (xi + 1.0) / 2.0], axis=1)
-    dlam = np.zeros((dim + 1, dim))
+    dlam = np.zeros((dim + 1, dim), dtype=xi.dtype)
     dlam[0, :] = -0.5
     for k in range(dim):
         dlam[k + 1, k] = 0.5
@@ -64,15 +69,16 @@ def lagrange_simplex(dim, P, targets):
     nodes = lattice(dim, P)
     lam_n, _ = _barycentric(nodes)
     Ibar = np.rint(lam_n * P).astype(int)                       # [n, d+1]
-    lam, dlam = _barycentric(np.asarray(targets, dtype=float))  # [t, d+1]
+    F = _working_type(targets)
+    lam, dlam = _barycentric(np.asarray(targets, dtype=F))      # [t, d+1]
     T, n = lam.shape[0], len(nodes)
-    L = np.ones((T, n))
-    dLdlam = np.zeros((T, n, dim + 1))
+    L = np.ones((T, n), dtype=F)
+    dLdlam = np.zeros((T, n, dim + 1), dtype=F)
     for i in range(n):
         fac = []
         for k in range(dim + 1):
-            f = np.ones(T)
-            df = np.zeros(T)
+            f = np.ones(T, dtype=F)
+            df = np.zeros(T, dtype=F)
             for m in range(Ibar[i, k]):
                 term = (P * lam[:, k] - m) / (Ibar[i, k] - m)
                 df = df * term + f * P / (Ibar[i, k] - m)
@@ -89,17 +95,25 @@ def lagrange_simplex(dim, P, targets):
     return L, dL
 
 
-def _cross(a, b):
-    return np.cross(a, b)
+def _det(A):
+    """Determinant of the trailing 2x2 or 3x3 blocks, by cofactors (any float type)."""
+    if A.shape[-1] == 2:
+        return A[..., 0, 0] * A[..., 1, 1] - A[..., 0, 1] * A[..., 1, 0]
+    return (A[..., 0, 0] * (A[..., 1, 1] * A[..., 2, 2] - A[..., 1, 2] * A[..., 2, 1])
+            - A[..., 0, 1] * (A[..., 1, 0] * A[..., 2, 2] - A[..., 1, 2] * A[..., 2, 0])
+            + A[..., 0, 2] * (A[..., 1, 0] * A[..., 2, 1] - A[..., 1, 1] * A[..., 2, 0]))
 
 
 class Geometry:
-    """Per-element geometric factors of a mesh of curved simplices."""
+    """Per-element geometric factors of a mesh of curved simplices, in the floating-point
+    type of the reference element.  ``perm`` (the facet-node permutations, integers) may be
+    given instead of being found by matching facets, e.g. for a sub-mesh whose outer
+    neighbours are absent."""
 
-    def __init__(self, ref, map_nodes, nbr_elem, nbr_face, pg=None):
+    def __init__(self, ref, map_nodes, nbr_elem, nbr_face, pg=None, perm=None):
         self.ref = ref
         dim, q = ref.dim, ref.q
-        X = np.asarray(map_nodes, dtype=float)          # [E, N*_pg, dim]
+        X = np.asarray(map_nodes, dtype=ref.dtype)      # [E, N*_pg, dim]
         E = X.shape[0]
         npg = X.shape[1]
         pg = pg if pg is not None else next(P for P in range(1, 40)
@@ -115,7 +129,7 @@ class Geometry:
         self.x_vol = x[:, :ref.Nq]
         self.x_fac = [x[:, ref.Nq + z * ref.Nqf: ref.Nq + (z + 1) * ref.Nqf] for z in range(ref.Nf)]
         if dim == 2:
-            G = np.empty(A.shape)
+            G = np.empty(A.shape, dtype=A.dtype)
             G[..., 0, 0] = A[..., 1, 1]
             G[..., 0, 1] = -A[..., 0, 1]
             G[..., 1, 0] = -A[..., 1, 0]
@@ -130,23 +144,26 @@ class Geometry:
         self.Jf = [np.linalg.norm(v, axis=-1) for v in self.Jn_fac]
         self.n_fac = [self.Jn_fac[z] / self.Jf[z][..., None] for z in range(ref.Nf)]
         # interpolated Jacobian determinant (degree pg) at volume nodes
-        lat = lattice(dim, pg)
+        lat = lattice(dim, pg, ref.dtype)
         _, dLl = lagrange_simplex(dim, pg, lat)
         Al = np.einsum("tik,eim->etmk", dLl, Xl)
-        detl = np.linalg.det(Al)
+        detl = _det(Al)
         Lv, _ = lagrange_simplex(dim, pg, ref.xi)
         self.J_vol = np.einsum("ti,ei->et", Lv, detl)
-        self.J_exact_vol = np.linalg.det(A[:, :ref.Nq])
+        self.J_exact_vol = _det(A[:, :ref.Nq])
         self.det_lattice = detl
         self.nbr_elem = np.asarray(nbr_elem)
         self.nbr_face = np.asarray(nbr_face)
-        self._match_facets()
+        if perm is None:
+            self._match_facets()
+        else:
+            self.perm = np.asarray(perm, dtype=np.int64)
 
     def _curl_metrics(self, X, pg, pts):
         ref = self.ref
         dim, q = ref.dim, ref.q
         Xl = X - X[:, :1, :]                              # element-local translation
-        inodes = lattice(dim, q + 1)
+        inodes = lattice(dim, q + 1, ref.dtype)
         Lm_i, dLm_i = lagrange_simplex(dim, pg, inodes)
         xi_ = np.einsum("ti,eid->etd", Lm_i, Xl)          # x at interpolation nodes
         gi = np.einsum("tik,eim->etmk", dLm_i, Xl)        # grad_xi x_m at interpolation nodes
@@ -156,7 +173,7 @@ class Geometry:
         _, dLq = lagrange_simplex(dim, q + 1, pts)        # [t, i, k]
         def curl(r):                                      # sum_i grad ell_i x r_i
             return np.einsum("tik,eil->etkl", dLq, r)     # outer; take the antisymmetric part below
-        out = np.empty((X.shape[0], len(pts), 3, 3))
+        out = np.empty((X.shape[0], len(pts), 3, 3), dtype=ref.dtype)
         for col, (r, sgn) in enumerate(((r1, -1.0), (r2, 1.0), (r3, 1.0))):
             T = curl(r)                                   # T[e,t,k,l] = sum_i d_k ell_i r_i,l
             c = np.stack([T[..., 1, 2] - T[..., 2, 1],

@@ -6,7 +6,7 @@ Modal multi-indices alpha in N(p) are ordered lexicographically with alpha_1
 slowest (the order the C ABI documents).
 """
 import numpy as np
-from .jacobi import jacobi_p
+from .jacobi import jacobi_p, _working_type
 
 
 def modal_indices(dim, p):
@@ -23,15 +23,17 @@ def modal_indices(dim, p):
 
 def pkd_eval(dim, p, eta):
     """phi_j(chi(eta)) for all modes j: shape [len(eta), N_p*]."""
-    eta = np.atleast_2d(np.asarray(eta, dtype=float))
+    T = _working_type(eta)
+    eta = np.atleast_2d(np.asarray(eta, dtype=T))
     idx = modal_indices(dim, p)
-    out = np.zeros((eta.shape[0], len(idx)))
+    out = np.zeros((eta.shape[0], len(idx)), dtype=T)
+    sqrt2 = np.sqrt(T(2))
     for j, a in enumerate(idx):
-        psi1 = np.sqrt(2.0) * jacobi_p(a[0], 0, 0, eta[:, 0])[a[0]]
+        psi1 = sqrt2 * jacobi_p(a[0], 0, 0, eta[:, 0])[a[0]]
         psi2 = (1 - eta[:, 1]) ** a[0] * jacobi_p(a[1], 2 * a[0] + 1, 0, eta[:, 1])[a[1]]
         val = psi1 * psi2
         if dim == 3:
-            psi3 = 2.0 * (1 - eta[:, 2]) ** (a[0] + a[1]) * jacobi_p(a[2], 2 * a[0] + 2 * a[1] + 2, 0, eta[:, 2])[a[2]]
+            psi3 = 2 * (1 - eta[:, 2]) ** (a[0] + a[1]) * jacobi_p(a[2], 2 * a[0] + 2 * a[1] + 2, 0, eta[:, 2])[a[2]]
             val = val * psi3
         out[:, j] = val
     return out

@@ -31,11 +31,17 @@ from . import euler
 
 
 class Discretization:
-    def __init__(self, dim, p, map_nodes, nbr_elem, nbr_face, flux="LF", gamma=euler.GAMMA):
+    """The discretisation of one mesh, in floating-point type ``dtype`` (FP64 by default;
+    np.longdouble for the extended-precision evaluation).  ``perm``: the facet-node
+    permutations, when known (otherwise found by matching facets)."""
+
+    def __init__(self, dim, p, map_nodes, nbr_elem, nbr_face, flux="LF", gamma=euler.GAMMA,
+                 dtype=float, perm=None):
         self.dim, self.p = dim, p
-        self.ref = RefElement(dim, p)
+        self.dtype = np.dtype(dtype).type
+        self.ref = RefElement(dim, p, self.dtype)
         self.V = vandermonde(self.ref, p)
-        self.geo = Geometry(self.ref, map_nodes, nbr_elem, nbr_face)
+        self.geo = Geometry(self.ref, map_nodes, nbr_elem, nbr_face, perm=perm)
         self.dissipation = (flux == "LF")
         self.gamma = gamma
         self.Np = self.V.shape[1]
@@ -104,8 +110,13 @@ class Discretization:
             out.append(euler.interface_flux(Utf[z][elems], ext, geo.n_fac[z][elems], self.dissipation, self.gamma))
         return out
 
-    def nodal_residual(self, um, route="dense", elems=None, chunk=16, return_count=False):
-        """r of Eq. (entropy_stable) for the elements ``elems``: [e, Nq, Nc]."""
+    def nodal_residual(self, um, route="dense", elems=None, chunk=16, return_count=False,
+                       return_scale=False):
+        """r of Eq. (entropy_stable) for the elements ``elems``: [e, Nq, Nc].
+
+        ``return_scale`` (sparse route): also return, per node and variable, the sum of the
+        absolute values of the terms that r adds up (every pair flux times its operator
+        entry, every facet-correction term, every lifted interface-flux term)."""
         if elems is None:
             elems = np.arange(self.E)
             w, Ut, Utf = self.states(um)
@@ -113,7 +124,7 @@ class Discretization:
             elems = np.asarray(elems)
             need = np.unique(np.concatenate([elems, self.geo.nbr_elem[elems].ravel()]))
             w, Ut, Utf = self.states(um, need if len(need) < self.E else None)
-        out = []
+        out, scales = [], []
         count = 0
         for s in range(0, len(elems), chunk):
             el = elems[s:s + chunk]
@@ -121,11 +132,14 @@ class Discretization:
             if route == "dense":
                 r = self._residual_dense(el, Ut, Utf, fstar)
             elif route == "sparse":
-                r, count = self._residual_sparse(el, Ut, Utf, fstar)
+                r, count, T = self._residual_sparse(el, Ut, Utf, fstar, return_scale)
+                scales.append(T)
             else:
                 raise ValueError(route)
             out.append(r)
         r = np.concatenate(out, axis=0)
+        if return_scale:
+            return r, np.concatenate(scales, axis=0)
         return (r, count) if return_count else r
 
     def _residual_dense(self, el, Ut, Utf, fstar):
@@ -150,11 +164,12 @@ class Discretization:
             r -= C1 + np.einsum("ji,ejc->eic", ref.R[z], g)
         return r
 
-    def _residual_sparse(self, el, Ut, Utf, fstar):
+    def _residual_sparse(self, el, Ut, Utf, fstar, want_scale=False):
         ref, geo, d = self.ref, self.geo, self.dim
         U = Ut[el]
         G = geo.G_vol[el]
         vol = np.zeros(U.shape, dtype=U.dtype)
+        T = np.zeros(U.shape, dtype=U.dtype)           # sums of |terms| (want_scale)
         count = 0
         for l in range(d):
             I, J = np.nonzero(np.triu(ref.S[l], 1))
@@ -163,6 +178,10 @@ class Discretization:
                 F = euler.ranocha_flux_dir(U[:, i], U[:, j], g, self.gamma)
                 vol[:, i] += ref.S[l][i, j] * F
                 vol[:, j] -= ref.S[l][i, j] * F
+                if want_scale:
+                    a = np.abs(ref.S[l][i, j] * F)
+                    T[:, i] += a
+                    T[:, j] += a
                 count += 1
         r = -vol
         for z in range(ref.Nf):
@@ -172,16 +191,35 @@ class Discretization:
             RtB = ref.R[z].T @ ref.B[z]
             C1 = np.zeros(U.shape, dtype=U.dtype)
             Ct1 = np.zeros(Uf.shape, dtype=U.dtype)
+            aC1 = np.zeros(U.shape, dtype=U.dtype)
+            aCt1 = np.zeros(Uf.shape, dtype=U.dtype)
             I, J = np.nonzero(RtB)
             for i, j in zip(I, J):
                 n = 0.5 * (JnV[:, i] + JnF[:, j])
                 C = RtB[i, j] * euler.ranocha_flux_dir(U[:, i], Uf[:, j], n, self.gamma)
                 C1[:, i] += C
                 Ct1[:, j] += C
+                if want_scale:
+                    aC1[:, i] += np.abs(C)
+                    aCt1[:, j] += np.abs(C)
                 count += 1
-            g = (ref.wf[z][None, :] * geo.Jf[z][el])[..., None] * fstar[z] - Ct1
+            bjf = (ref.wf[z][None, :] * geo.Jf[z][el])[..., None] * fstar[z]
+            g = bjf - Ct1
             r -= C1 + np.einsum("ji,ejc->eic", ref.R[z], g)
-        return r, count
+            if want_scale:
+                T += aC1 + np.einsum("ji,ejc->eic", np.abs(ref.R[z]), np.abs(bjf) + aCt1)
+        return r, count, T
+
+    def term_scale(self, um, elems):
+        """Scale of the rounding of d u~/dt: the sums of |terms| of the nodal residual
+        (nodal_residual(return_scale=True)) carried through |V|^T, |V| diag(W/J) |V|^T
+        of Eq. (dudt_modal): [e, Nc, Np], an upper bound of |d u~/dt| entry by entry."""
+        elems = np.asarray(elems)
+        _, T = self.nodal_residual(um, "sparse", elems, return_scale=True)
+        aV = np.abs(self.V)
+        y = np.einsum("ij,eic->ejc", aV, T)
+        t = np.einsum("ij,ejc->eic", aV, y) * (self.ref.w[None, :] / self.geo.J_vol[elems])[..., None]
+        return np.transpose(np.einsum("ij,eic->ejc", aV, t), (0, 2, 1))
 
     def rhs(self, um, route="dense", elems=None, chunk=16):
         """d u~/dt of Eq. (dudt_modal) in the ABI layout [e, Nc, Np]."""
@@ -199,7 +237,7 @@ class Discretization:
         Nb = Nq + Nf * Nqf
         Qbar = []
         for l in range(d):
-            Q = np.zeros((Nb, Nb))
+            Q = np.zeros((Nb, Nb), dtype=self.dtype)
             Q[:Nq, :Nq] = ref.S[l]
             for z in range(Nf):
                 s = slice(Nq + z * Nqf, Nq + (z + 1) * Nqf)
