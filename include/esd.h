@@ -27,7 +27,12 @@
  *   launch.  A non-admissible state (rho <= 0, p <= 0 or non-finite values at a
  *   quadrature node) sets a device flag that esd_mesh_check() reports as
  *   ESD_ERR_STATE.
- * - A mesh handle may be used from one host thread at a time.
+ * - A mesh handle may be used from one host thread at a time.  It belongs to the
+ *   device that was current when it was created (its tables and workspace live there):
+ *   every call that touches the device must be made with that device current, else it
+ *   returns ESD_ERR_ARG before enqueuing anything.
+ * - Test and measurement hooks (timing one kernel, the FP64 peak, host-table export,
+ *   failure-path probes) are declared separately in esd_test.h.
  */
 #ifndef ESD_H
 #define ESD_H
@@ -106,9 +111,13 @@ esd_status esd_mesh_destroy(esd_mesh mesh);
 esd_status esd_mesh_info(esd_mesh mesh, esd_info* out);
 
 /* Synchronize the stream, then report (and clear) the device error flag: ESD_OK,
- * ESD_ERR_TIMEOUT (a shared-memory staging copy did not complete within its bounded
- * wait of about one second; that block skipped its work) or ESD_ERR_STATE (a
- * non-admissible state). */
+ * ESD_ERR_TIMEOUT or ESD_ERR_STATE (a non-admissible state).
+ * ESD_ERR_TIMEOUT means that a shared-memory staging copy of some block did not complete
+ * within its bounded wait of about one second: that block skipped its work (its outputs
+ * hold stale values) after waiting once more, for the same time, for its copies to land.
+ * If they had still not landed, a copy may complete into shared memory after the block
+ * has exited.  Treat the outputs of every call since the previous check as invalid, and a
+ * device that times out as unreliable for the rest of the process. */
 esd_status esd_mesh_check(esd_mesh mesh, void* stream);
 
 /* Physical coordinates of the volume quadrature nodes, HOST output
@@ -144,8 +153,10 @@ esd_status esd_rhs(esd_mesh mesh, const double* u, double* dudt, void* stream);
  * - Limit: the mesh needs n_elem * ((dim+5) * (N_q + N_f*N_fq) + N_f*N_fq) doubles of
  *   scratch (about 15 KB per element for tetrahedra at p = 4, 2.4 KB for triangles at
  *   p = 4); larger meshes are rejected with ESD_ERR_UNSUPPORTED before any launch.
- * - The first call on a device looks up the array's device address (once per device,
- *   with that device current); make that first call before any stream capture.
+ * - Each call looks up the array's device address on the current device (the mesh's
+ *   device: see above).  The first call on a device also loads the library's device
+ *   code there if nothing has loaded it yet; make that first call before any stream
+ *   capture.
  * - Every call shares the one array and leaves the last call's contents in it.  Nothing
  *   in it needs to start at zero (each call overwrites every value it reads), but calls
  *   that overlap on the GPU (different streams, or concurrent host threads) race on it.
@@ -213,49 +224,9 @@ esd_status esd_autotune(esd_mesh mesh, const double* u, void* stream);
 enum { ESD_TUNE_PROJECT = 1, ESD_TUNE_RESIDUAL = 2, ESD_TUNE_ADJOINT = 4, ESD_TUNE_ALL = 7 };
 esd_status esd_autotune_kernels(esd_mesh mesh, const double* u, int kernels, void* stream);
 
-/* Measurement hook: launch one kernel of the esd_rhs pipeline alone, so that it can be
- * timed with events on `stream`.  stage 0: the projection kernel on u (entropy projection
- * and entropy-projected states at all nodes, written to the handle's workspace; `out`
- * unused, may be NULL); stage 1: the residual kernel on the workspace states left by the
- * last stage-0 launch, writing d u~/dt to `out` (device).  esd_rhs == stage 0 then 1. */
-esd_status esd_launch_stage(esd_mesh mesh, int stage, const double* u, double* out, void* stream);
-
-/* Measurement helper: sustained FP64 FMA throughput of this device, in FP64
- * operations (1 FMA = 2) per second, measured with a register-resident FMA chain
- * on the given stream (synchronous). */
-esd_status esd_measure_fp64_peak(double* flops_per_s, void* stream);
-
 /* Per-element sizes for a (dim, p) pair without building a mesh (n_elem = 0,
  * device_bytes = 0, launch fields 0).  Host only. */
 esd_status esd_ref_info(int dim, int p, esd_info* out);
-
-/* Test hook: run only the host part of esd_mesh_create (no device is touched) and
- * copy selected host tables out.  Every output is optional (NULL skips it); sizes,
- * with the library's internal node order (volume node c1 + n*(c2 + n*c3), facet
- * node zeta*Nqf + a + n*b, see the kernels for the pair order):
- *   wj [n_elem][N_q] (W J), bj [n_elem][N_f*Nqf] (B J^(kappa,zeta)),
- *   nrm [n_elem][dim][N_f*Nqf] (unit normals), vdir [n_elem][vol_pairs*dim],
- *   fdir [n_elem][facet_pairs*dim] (pair directions), nbr [n_elem][N_f*Nqf]
- *   (neighbour element), nbr_node (neighbour facet node), xvol [n_elem][N_q][dim]. */
-esd_status esd_debug_host_setup(const esd_mesh_desc* desc, double* wj, double* bj, double* nrm, double* vdir,
-                                double* fdir, int32_t* nbr, int32_t* nbr_node, double* xvol);
-
-/* Test hook: y = log(x) (which = 0) or exp(x) (which = 1) elementwise with the library's
- * table-driven device implementations; x, y device arrays of n doubles. */
-esd_status esd_debug_math(int which, const double* x, double* y, int64_t n, void* stream);
-
-/* Host-side audit (no device needed): for every supported (dim, p), the shared-memory
- * layouts of the residual and adjoint kernels are in bounds and disjoint where live
- * together, bulk copies are 16-byte sized and aligned, and the default launch shapes fit
- * one CTA.  ESD_OK, or ESD_ERR_UNSUPPORTED with the first violation in esd_last_error(). */
-esd_status esd_debug_check_layouts(void);
-
-/* Test hook for the failure path of the bounded waits (not in the paper): launches one
- * block that waits on a shared-memory barrier that nothing completes; after `seconds`
- * (0 < seconds <= 10) the wait gives up and sets the mesh's error flag, so that the next
- * esd_mesh_check returns ESD_ERR_TIMEOUT.  The kernels' staging copies use the same
- * bounded wait (about one second). */
-esd_status esd_debug_staging_timeout(esd_mesh mesh, double seconds, void* stream);
 
 const char* esd_status_string(esd_status s);
 const char* esd_last_error(void);

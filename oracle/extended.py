@@ -14,7 +14,8 @@ included.
 
 Only the sampled elements and their facet neighbours (whose traces enter the interface
 flux) are built, as a sub-mesh; its facet-node permutations (integers) are taken from the
-FP64 discretisation of the whole mesh.
+FP64 discretisation of the whole mesh, or matched within the sub-mesh
+(sub_discretization, which serves in FP64 too when the whole mesh is too large to build).
 """
 import numpy as np
 
@@ -36,6 +37,21 @@ def submesh(nbr_elem, elems):
     own = np.broadcast_to(np.arange(len(need))[:, None], pos.shape)
     loc = np.where(inside, pos, own).astype(np.int64)
     return need, loc, np.searchsorted(need, elems)
+
+
+def sub_discretization(dim, p, map_nodes, nbr_elem, nbr_face, elems, flux="LF", gamma=None,
+                       dtype=EXT):
+    """(discretisation of the sub-mesh around ``elems`` in type ``dtype``, need, local indices
+    of elems), built from the mesh arrays alone (no geometry of the whole mesh): facets
+    between two sub-mesh elements are matched as usual, the outer facets of the neighbours
+    are left unmatched (never read)."""
+    need, loc, local = submesh(nbr_elem, elems)
+    unmatched = loc == np.arange(len(need))[:, None]
+    X = np.asarray(map_nodes, dtype=np.float64)[need].astype(dtype)
+    kw = {} if gamma is None else dict(gamma=gamma)
+    Dx = Discretization(dim, p, X, loc, np.asarray(nbr_face)[need], flux=flux, dtype=dtype,
+                        unmatched=unmatched, **kw)
+    return Dx, need, local
 
 
 def discretization(D64, map_nodes, elems, dtype=EXT, flux=None):
@@ -61,7 +77,7 @@ def rhs_and_scale(D64, map_nodes, um, elems, dtype=EXT):
     Discretization.term_scale, the sums of |terms| carried through the modal transforms."""
     Dx, need, local = discretization(D64, map_nodes, elems, dtype)
     umx = np.asarray(um, dtype=np.float64)[need].astype(dtype)
-    return Dx.rhs(umx, "sparse", elems=local), Dx.term_scale(umx, local)
+    return Dx.rhs(umx, "sparse", elems=local, return_scale=True)
 
 
 def project_entropy(D64, map_nodes, um, elems, dtype=EXT):
@@ -69,3 +85,14 @@ def project_entropy(D64, map_nodes, um, elems, dtype=EXT):
     Dx, need, local = discretization(D64, map_nodes, elems, dtype)
     umx = np.asarray(um, dtype=np.float64)[need].astype(dtype)
     return Dx.project_entropy(umx, local)
+
+
+def local_vjp(D64, map_nodes, um, cot, e, dtype=EXT):
+    """(J^T cot) restricted to the modes of element e (oracle.jacobian.local_vjp_batched) in
+    extended precision, on the sub-mesh of e's neighbours and their neighbours."""
+    from .jacobian import local_vjp_batched
+    nbr = D64.geo.nbr_elem
+    nb = np.unique(np.concatenate([[e], nbr[e]]))
+    ring = np.unique(np.concatenate([nb, nbr[nb].ravel()]))
+    Dx, need, _ = discretization(D64, map_nodes, ring, dtype)
+    return local_vjp_batched(Dx, np.asarray(um)[need], np.asarray(cot)[need], int(np.searchsorted(need, e)))

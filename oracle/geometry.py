@@ -107,10 +107,11 @@ def _det(A):
 class Geometry:
     """Per-element geometric factors of a mesh of curved simplices, in the floating-point
     type of the reference element.  ``perm`` (the facet-node permutations, integers) may be
-    given instead of being found by matching facets, e.g. for a sub-mesh whose outer
-    neighbours are absent."""
+    given instead of being found by matching facets.  ``unmatched`` ([E, N_f] bool) marks
+    facets whose neighbour is not part of this (sub-)mesh: they are not matched and their
+    permutation (the identity) must not be used."""
 
-    def __init__(self, ref, map_nodes, nbr_elem, nbr_face, pg=None, perm=None):
+    def __init__(self, ref, map_nodes, nbr_elem, nbr_face, pg=None, perm=None, unmatched=None):
         self.ref = ref
         dim, q = ref.dim, ref.q
         X = np.asarray(map_nodes, dtype=ref.dtype)      # [E, N*_pg, dim]
@@ -155,7 +156,7 @@ class Geometry:
         self.nbr_elem = np.asarray(nbr_elem)
         self.nbr_face = np.asarray(nbr_face)
         if perm is None:
-            self._match_facets()
+            self._match_facets(unmatched)
         else:
             self.perm = np.asarray(perm, dtype=np.int64)
 
@@ -182,7 +183,7 @@ class Geometry:
             out[..., :, col] = sgn * c
         return out
 
-    def _match_facets(self):
+    def _match_facets(self, unmatched=None):
         ref = self.ref
         n, dim = ref.q + 1, ref.dim
         if dim == 2:
@@ -193,6 +194,9 @@ class Geometry:
         self.perm = np.zeros((self.E, ref.Nf, ref.Nqf), dtype=np.int64)
         for e in range(self.E):
             for z in range(ref.Nf):
+                if unmatched is not None and unmatched[e, z]:
+                    self.perm[e, z] = cands[0]
+                    continue
                 e2, z2 = int(self.nbr_elem[e, z]), int(self.nbr_face[e, z])
                 xa, xb = self.x_fac[z][e], self.x_fac[z2][e2]
                 scale = np.max(np.abs(xa - xa.mean(0))) + 1e-300

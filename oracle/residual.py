@@ -33,15 +33,16 @@ from . import euler
 class Discretization:
     """The discretisation of one mesh, in floating-point type ``dtype`` (FP64 by default;
     np.longdouble for the extended-precision evaluation).  ``perm``: the facet-node
-    permutations, when known (otherwise found by matching facets)."""
+    permutations, when known (otherwise found by matching facets); ``unmatched``: facets
+    whose neighbour is outside this (sub-)mesh (see Geometry)."""
 
     def __init__(self, dim, p, map_nodes, nbr_elem, nbr_face, flux="LF", gamma=euler.GAMMA,
-                 dtype=float, perm=None):
+                 dtype=float, perm=None, unmatched=None):
         self.dim, self.p = dim, p
         self.dtype = np.dtype(dtype).type
         self.ref = RefElement(dim, p, self.dtype)
         self.V = vandermonde(self.ref, p)
-        self.geo = Geometry(self.ref, map_nodes, nbr_elem, nbr_face, perm=perm)
+        self.geo = Geometry(self.ref, map_nodes, nbr_elem, nbr_face, perm=perm, unmatched=unmatched)
         self.dissipation = (flux == "LF")
         self.gamma = gamma
         self.Np = self.V.shape[1]
@@ -216,17 +217,24 @@ class Discretization:
         of Eq. (dudt_modal): [e, Nc, Np], an upper bound of |d u~/dt| entry by entry."""
         elems = np.asarray(elems)
         _, T = self.nodal_residual(um, "sparse", elems, return_scale=True)
+        return self._modal_scale(T, elems)
+
+    def _modal_scale(self, T, elems):
         aV = np.abs(self.V)
         y = np.einsum("ij,eic->ejc", aV, T)
         t = np.einsum("ij,ejc->eic", aV, y) * (self.ref.w[None, :] / self.geo.J_vol[elems])[..., None]
         return np.transpose(np.einsum("ij,eic->ejc", aV, t), (0, 2, 1))
 
-    def rhs(self, um, route="dense", elems=None, chunk=16):
-        """d u~/dt of Eq. (dudt_modal) in the ABI layout [e, Nc, Np]."""
+    def rhs(self, um, route="dense", elems=None, chunk=16, return_scale=False):
+        """d u~/dt of Eq. (dudt_modal) in the ABI layout [e, Nc, Np].  With ``return_scale``
+        (sparse route) also the term scale of each output (see term_scale)."""
         elems = np.arange(self.E) if elems is None else np.asarray(elems)
-        r = self.nodal_residual(um, route, elems, chunk)
+        r = self.nodal_residual(um, route, elems, chunk, return_scale=return_scale)
+        if return_scale:
+            r, T = r
         y = np.einsum("ij,eic->ejc", self.V, r)
-        return np.transpose(self.minv(y, elems), (0, 2, 1))
+        dudt = np.transpose(self.minv(y, elems), (0, 2, 1))
+        return (dudt, self._modal_scale(T, elems)) if return_scale else dudt
 
     # ---- hybridized route (Section 6) -------------------------------------------------
     def rhs_hybridized(self, um, elems=None):

@@ -1,4 +1,4 @@
-"""Python binding of the esd C-ABI library (include/esd.h).
+"""Python binding of the esd C-ABI library (include/esd.h; test hooks in include/esd_test.h).
 
 Argument marshalling only: every step of the computation runs in the CUDA
 kernels of libesd.so.  Torch tensors provide device memory and streams.  The
@@ -72,6 +72,7 @@ SYMBOLS = {
     "esd_debug_check_layouts": ([], ctypes.c_int),
     "esd_debug_math": ([ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p],
                        ctypes.c_int),
+    "esd_debug_set_mesh_device": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
     "esd_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "esd_last_error": ([], ctypes.c_char_p),
 }

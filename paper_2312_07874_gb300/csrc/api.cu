@@ -58,6 +58,19 @@ esd_status check_dev(const void* p, const char* name) {
   if (reinterpret_cast<uintptr_t>(p) % 8 != 0) return fail(ESD_ERR_ARG, std::string(name) + " is not 8-byte aligned");
   return ESD_OK;
 }
+
+// Every device-side call on a mesh must run with the mesh's own device current: its
+// tables and workspace live there, and a launch on another device would read them
+// through peer mappings (or fault).  Checked before anything is enqueued.
+esd_status check_device(int mesh_device) {
+  int cur = -1;
+  cudaError_t e = cudaGetDevice(&cur);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (cur != mesh_device)
+    return fail(ESD_ERR_ARG, "the mesh was created on device " + std::to_string(mesh_device) + " but device " +
+                                 std::to_string(cur) + " is current");
+  return ESD_OK;
+}
 }  // namespace
 
 // Captured RK4 (and batch) graphs kept per handle; the oldest is dropped beyond this.
@@ -73,6 +86,7 @@ struct GraphEntry {
 
 struct esd_mesh_s {
   int dim = 0, p = 0, nc = 0;
+  int device = -1;             // the device current at esd_mesh_create; it owns every allocation
   int64_t E = 0;
   RefTables ref;
   std::vector<double> xvol;
@@ -150,7 +164,11 @@ esd_status esd_mesh_create(const esd_mesh_desc* d, esd_mesh* out) {
   std::string err;
   esd_status st = build_host_mesh(*d, &H, &err);
   if (st != ESD_OK) return fail(st, err);
+  int device = -1;
+  cudaError_t de = cudaGetDevice(&device);
+  if (de != cudaSuccess) return cuda_fail(de, "cudaGetDevice");
   esd_mesh m = new esd_mesh_s();
+  m->device = device;
   m->dim = d->dim;
   m->p = d->p;
   m->nc = d->dim + 2;
@@ -263,6 +281,7 @@ esd_status esd_mesh_info(esd_mesh m, esd_info* o) {
 
 esd_status esd_mesh_check(esd_mesh m, void* stream) {
   if (!m) return fail(ESD_ERR_ARG, "null mesh");
+  if (esd_status ds = check_device(m->device)) return ds;
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
@@ -280,9 +299,16 @@ esd_status esd_mesh_check(esd_mesh m, void* stream) {
 
 esd_status esd_debug_staging_timeout(esd_mesh m, double seconds, void* stream) {
   if (!m) return fail(ESD_ERR_ARG, "null mesh");
+  if (esd_status ds = check_device(m->device)) return ds;
   if (!(seconds > 0.0) || seconds > 10.0) return fail(ESD_ERR_ARG, "seconds must be in (0, 10]");
   cudaError_t e = launch_staging_timeout_probe(m->M.flag, seconds, (cudaStream_t)stream);
   return e ? cuda_fail(e, "timeout probe launch") : ESD_OK;
+}
+
+esd_status esd_debug_set_mesh_device(esd_mesh m, int device) {
+  if (!m) return fail(ESD_ERR_ARG, "null mesh");
+  m->device = device;
+  return ESD_OK;
 }
 
 esd_status esd_mesh_volume_nodes(esd_mesh m, double* x) {
@@ -294,6 +320,7 @@ esd_status esd_mesh_volume_nodes(esd_mesh m, double* x) {
 esd_status esd_l2_project(esd_mesh m, const double* un, double* um, void* stream) {
   ESD_RANGE("esd_l2_project");
   if (!m) return fail(ESD_ERR_ARG, "null mesh");
+  if (esd_status ds = check_device(m->device)) return ds;
   esd_status st;
   if ((st = check_dev(un, "u_nodal")) || (st = check_dev(um, "u_modal"))) return st;
   cudaError_t e = launch_l2_project(m->R, m->M, un, um, (cudaStream_t)stream);
@@ -303,6 +330,7 @@ esd_status esd_l2_project(esd_mesh m, const double* un, double* um, void* stream
 esd_status esd_project_entropy(esd_mesh m, const double* u, double* w, void* stream) {
   ESD_RANGE("esd_project_entropy");
   if (!m) return fail(ESD_ERR_ARG, "null mesh");
+  if (esd_status ds = check_device(m->device)) return ds;
   esd_status st;
   if ((st = check_dev(u, "u")) || (st = check_dev(w, "w_modal"))) return st;
   cudaError_t e = launch_project(m->R, m->M, m->L, u, w, (cudaStream_t)stream);
@@ -312,6 +340,7 @@ esd_status esd_project_entropy(esd_mesh m, const double* u, double* w, void* str
 esd_status esd_rhs(esd_mesh m, const double* u, double* dudt, void* stream) {
   ESD_RANGE("esd_rhs");
   if (!m) return fail(ESD_ERR_ARG, "null mesh");
+  if (esd_status ds = check_device(m->device)) return ds;
   esd_status st;
   if ((st = check_dev(u, "u")) || (st = check_dev(dudt, "dudt"))) return st;
   if (u == dudt) return fail(ESD_ERR_ARG, "u and dudt must not alias");
@@ -351,6 +380,7 @@ static cudaError_t rk_sequence(esd_mesh m, double* u, double dt, double* ck, cud
 esd_status esd_rk_step(esd_mesh m, double* u, double dt, double* ck, void* stream) {
   ESD_RANGE("esd_rk_step");
   if (!m) return fail(ESD_ERR_ARG, "null mesh");
+  if (esd_status ds = check_device(m->device)) return ds;
   esd_status st;
   if ((st = check_dev(u, "u"))) return st;
   if (ck && (st = check_dev(ck, "stage_ckpt"))) return st;
@@ -390,6 +420,7 @@ esd_status esd_rk_step(esd_mesh m, double* u, double dt, double* ck, void* strea
 esd_status esd_diagnostics(esd_mesh m, const double* u, double* out, void* stream) {
   ESD_RANGE("esd_diagnostics");
   if (!m) return fail(ESD_ERR_ARG, "null mesh");
+  if (esd_status ds = check_device(m->device)) return ds;
   esd_status st;
   if ((st = check_dev(u, "u")) || (st = check_dev(out, "out"))) return st;
   cudaStream_t s = (cudaStream_t)stream;
@@ -406,6 +437,7 @@ esd_status esd_diagnostics(esd_mesh m, const double* u, double* out, void* strea
 esd_status esd_integrals(esd_mesh m, const double* u, double* out, void* stream) {
   ESD_RANGE("esd_integrals");
   if (!m) return fail(ESD_ERR_ARG, "null mesh");
+  if (esd_status ds = check_device(m->device)) return ds;
   esd_status st;
   if ((st = check_dev(u, "u")) || (st = check_dev(out, "out"))) return st;
   cudaStream_t s = (cudaStream_t)stream;
@@ -418,6 +450,7 @@ esd_status esd_integrals(esd_mesh m, const double* u, double* out, void* stream)
 esd_status esd_rhs_vjp(esd_mesh m, const double* u, const double* cot, double* grad, void* stream) {
   ESD_RANGE("esd_rhs_vjp");
   if (!m) return fail(ESD_ERR_ARG, "null mesh");
+  if (esd_status ds = check_device(m->device)) return ds;
   esd_status st;
   if ((st = check_dev(u, "u")) || (st = check_dev(cot, "cot")) || (st = check_dev(grad, "grad"))) return st;
   if (grad == u || grad == cot) return fail(ESD_ERR_ARG, "grad must not alias u or cot");
@@ -433,6 +466,7 @@ esd_status esd_rhs_vjp(esd_mesh m, const double* u, const double* cot, double* g
 esd_status esd_rk_step_vjp(esd_mesh m, const double* ck, double dt, const double* co, double* ci, void* stream) {
   ESD_RANGE("esd_rk_step_vjp");
   if (!m) return fail(ESD_ERR_ARG, "null mesh");
+  if (esd_status ds = check_device(m->device)) return ds;
   esd_status st;
   if ((st = check_dev(ck, "stage_ckpt")) || (st = check_dev(co, "cot_out")) || (st = check_dev(ci, "cot_in")))
     return st;
@@ -503,6 +537,8 @@ esd_status esd_batch_create(const esd_mesh* meshes, int n, esd_batch* out) {
   if (!meshes || n <= 0 || !out) return fail(ESD_ERR_ARG, "invalid batch arguments");
   for (int i = 0; i < n; ++i)
     if (!meshes[i]) return fail(ESD_ERR_ARG, "null mesh in batch");
+  for (int i = 0; i < n; ++i)
+    if (esd_status ds = check_device(meshes[i]->device)) return ds;
   esd_batch b = new esd_batch_s();
   b->meshes.assign(meshes, meshes + n);
   const int sms = sm_count();
@@ -700,6 +736,8 @@ static esd_status batch_run(esd_batch b, int kind, const std::vector<const doubl
 }
 
 esd_status esd_batch_rhs(esd_batch b, const double* const* u, double* const* dudt, void* stream) {
+  if (b && !b->meshes.empty())
+    if (esd_status ds = check_device(b->meshes[0]->device)) return ds;
   ESD_RANGE("esd_batch_rhs");
   if (!b || !u || !dudt) return fail(ESD_ERR_ARG, "null argument");
   const size_t n = b->meshes.size();
@@ -715,6 +753,8 @@ esd_status esd_batch_rhs(esd_batch b, const double* const* u, double* const* dud
 }
 
 esd_status esd_batch_rk_step(esd_batch b, double* const* u, const double* dt, void* stream) {
+  if (b && !b->meshes.empty())
+    if (esd_status ds = check_device(b->meshes[0]->device)) return ds;
   ESD_RANGE("esd_batch_rk_step");
   if (!b || !u || !dt) return fail(ESD_ERR_ARG, "null argument");
   const size_t n = b->meshes.size();
@@ -741,32 +781,23 @@ constexpr size_t kStaticScratchBytes = size_t(32) << 20;   // 32 MiB
 constexpr size_t kStaticScratchDoubles = kStaticScratchBytes / sizeof(double);
 static __device__ __align__(256) double g_static_scratch[kStaticScratchDoubles];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_scratch_mutex;
-double* g_scratch_ptr[kMaxDevices] = {};
-
 // Device address of g_static_scratch on the current device.  In host code the
-// symbol's name is only a host-side stand-in, so the address is looked up once per
-// device (with that device current) and cached.
+// symbol's name is only a host-side stand-in, so the address is looked up with the
+// device current.  The lookup is repeated on every call (it is a host-side table lookup
+// once the library's device code is loaded on the device): an address cached across calls
+// would go stale if the device's context were reset and the code reloaded elsewhere.
 esd_status static_scratch_address(double** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-  if (dev < 0 || dev >= kMaxDevices) return fail(ESD_ERR_UNSUPPORTED, "device index out of range for the static scratch");
-  std::lock_guard<std::mutex> lock(g_scratch_mutex);
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_static_scratch);
-    if (e != cudaSuccess || p == nullptr) return cuda_fail(e, "cudaGetSymbolAddress(static scratch)");
-    g_scratch_ptr[dev] = static_cast<double*>(p);
-  }
-  *out = g_scratch_ptr[dev];
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+  if (e != cudaSuccess || p == nullptr) return cuda_fail(e, "cudaGetSymbolAddress(static scratch)");
+  *out = static_cast<double*>(p);
   return ESD_OK;
 }
 }  // namespace
 
 esd_status esd_rhs_static_scratch(esd_mesh m, const double* u, double* dudt, void* stream) {
   if (!m) return fail(ESD_ERR_ARG, "null mesh");
+  if (esd_status ds = check_device(m->device)) return ds;
   esd_status st;
   if ((st = check_dev(u, "u")) || (st = check_dev(dudt, "dudt"))) return st;
   if (u == dudt) return fail(ESD_ERR_ARG, "u and dudt must not alias");
@@ -829,6 +860,7 @@ esd_status esd_autotune(esd_mesh m, const double* u, void* stream) {
 esd_status esd_autotune_kernels(esd_mesh m, const double* u, int kernels, void* stream) {
   ESD_RANGE("esd_autotune_kernels");
   if (!m) return fail(ESD_ERR_ARG, "null mesh");
+  if (esd_status ds = check_device(m->device)) return ds;
   if (kernels & ~ESD_TUNE_ALL) return fail(ESD_ERR_ARG, "unknown kernel bits");
   esd_status st;
   if ((st = check_dev(u, "u"))) return st;
@@ -941,6 +973,7 @@ esd_status esd_autotune_kernels(esd_mesh m, const double* u, int kernels, void* 
 
 esd_status esd_launch_stage(esd_mesh m, int stage, const double* u, double* out, void* stream) {
   if (!m) return fail(ESD_ERR_ARG, "null mesh");
+  if (esd_status ds = check_device(m->device)) return ds;
   cudaStream_t s = (cudaStream_t)stream;
   esd_status st;
   if (stage == 0) {

@@ -9,7 +9,7 @@
 
 #include <cuda_runtime.h>
 
-#include "esd.h"
+#include "esd_test.h"   // the product ABI (esd.h) and the test hooks
 
 namespace esd {
 

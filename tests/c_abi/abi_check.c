@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include "esd.h"
+#include "esd_test.h"
 
 int main(void) {
   esd_info info;

@@ -1,6 +1,10 @@
-"""Batched persistent execution of many meshes (esd_batch_*) against the plain per-mesh path."""
+"""Batched persistent execution of many meshes (esd_batch_*): against the oracle (sampled
+elements of every mesh of a mixed batch; whole small meshes for the RK4 step) and against
+the plain per-mesh path (bitwise)."""
 import numpy as np
 import pytest
+
+from gpu_common import check_parity, flat_case, rel_err_per_var
 
 pytestmark = pytest.mark.gpu
 
@@ -8,7 +12,7 @@ MIX = [(2, 3, 2, "vortex"), (2, 4, 4, "vortex"), (3, 3, 2, "tgv"), (2, 3, 7, "vo
        (3, 4, 1, "tgv"), (3, 3, 9, "tgv"), (3, 3, 3, "tgv")]
 
 
-def _meshes():
+def _meshes(with_arrays=False):
     import torch
     import esd_inputs as I
     import paper_2312_07874_gb300 as E
@@ -21,8 +25,67 @@ def _meshes():
         un = np.ascontiguousarray(np.transpose(I.config_state_fn(dim, L, state)(x), (0, 2, 1)))
         u = gm.l2_project(torch.from_numpy(un).cuda())
         u += 1e-3 * torch.from_numpy(I.seeded_normal(30 + k, tuple(u.shape), 1.0)).cuda()
-        out.append((gm, u))
+        out.append((gm, u, mesh, X) if with_arrays else (gm, u))
     return out
+
+
+def test_batch_rhs_against_oracle():
+    """One esd_batch_rhs over the mixed batch (triangles and tetrahedra, p = 1..9, element
+    counts that leave ragged last tiles): every mesh's output on sampled elements (its last
+    element included) against the oracle, FP64 and, up to p = 7, long double."""
+    import torch
+    import paper_2312_07874_gb300 as E
+    from oracle import extended
+    ms = _meshes(with_arrays=True)
+    b = E.esd_batch_create([m.handle for m, *_ in ms])
+    outs = [torch.empty_like(u) for _, u, *_ in ms]
+    E.esd_batch_rhs(b, [u for _, u, *_ in ms], outs)
+    torch.cuda.synchronize()
+    for k, ((gm, u, mesh, X), o) in enumerate(zip(ms, outs)):
+        gm.check()
+        dim, M, p, state = MIX[k]
+        rng = np.random.default_rng(60 + k)
+        sample = np.unique(np.append(rng.choice(mesh.n_elem, 3, replace=False), mesh.n_elem - 1))
+        Ds, need, local = extended.sub_discretization(dim, p, X, mesh.nbr_elem, mesh.nbr_face, sample,
+                                                      dtype=np.float64)
+        um = u.cpu().numpy()[need]
+        check_parity(f"batch rhs mesh {k}: dim={dim} M={M} p={p} {state}", o.cpu().numpy()[sample], Ds,
+                     X[need], um, elems=local, flat=flat_case(state, p), n_exact=1 if p <= 7 else 0, seed=k)
+    E.esd_batch_destroy(b)
+
+
+def test_batch_rk_step_against_oracle():
+    """One esd_batch_rk_step over a mixed batch of whole small meshes against the oracle's
+    RK4 step of each mesh (increments, 1e-12 relative per variable: well-conditioned states)."""
+    import torch
+    import esd_inputs as I
+    import paper_2312_07874_gb300 as E
+    from oracle.residual import Discretization
+    from oracle.timestep import rk4_step
+    mix = [(2, 3, 2, "vortex"), (3, 3, 1, "density_wave"), (2, 4, 3, "vortex"), (3, 3, 2, "density_wave")]
+    L = 2 * np.pi
+    Ds, gms, us, ums, dts = [], [], [], [], []
+    for k, (dim, M, p, state) in enumerate(mix):
+        mesh, X = I.config_mesh(dim, M, L, p, True)
+        D = Discretization(dim, p, X, mesh.nbr_elem, mesh.nbr_face)
+        um = np.einsum("ij,i,eic->ecj", D.V, D.ref.w, I.config_state_fn(dim, L, state)(D.geo.x_vol))
+        um = np.ascontiguousarray(um + I.seeded_normal(70 + k, um.shape, 1e-3))
+        Ds.append(D)
+        gms.append(E.Mesh(dim, p, X, mesh.nbr_elem, mesh.nbr_face))
+        ums.append(um)
+        us.append(torch.from_numpy(um).cuda())
+        dts.append(2e-3 * (1 + 0.25 * k))
+    b = E.esd_batch_create([m.handle for m in gms])
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        E.esd_batch_rk_step(b, us, dts)
+    s.synchronize()
+    for D, gm, u, um, dt in zip(Ds, gms, us, ums, dts):
+        gm.check()
+        ref = rk4_step(lambda v: D.rhs(v, "sparse"), um, dt)
+        err = rel_err_per_var(u.cpu().numpy() - um, ref - um)
+        assert np.all(err < 1e-12), err
+    E.esd_batch_destroy(b)
 
 
 def test_batch_rhs_equals_per_mesh():

@@ -19,7 +19,8 @@ pytestmark = pytest.mark.skipif(not os.path.exists(LIB), reason="libesd.so not b
 
 
 def test_library_exports_every_declared_symbol():
-    header = open(os.path.join(ROOT, "include", "esd.h")).read()
+    inc = os.path.join(ROOT, "include")
+    header = "".join(open(os.path.join(inc, f)).read() for f in sorted(os.listdir(inc)) if f.endswith(".h"))
     names = set(re.findall(r"\b(esd_[a-z0-9_]+)\s*\(", header))
     lib = ctypes.CDLL(LIB)
     missing = [n for n in sorted(names) if not hasattr(lib, n)]

@@ -69,3 +69,48 @@ def test_rk4_jvp_against_differences():
     f = lambda x: rk4_step(lambda y: D.rhs(y, "sparse"), x, dt)
     fd = (f(um + h * v) - f(um - h * v)) / (2 * h)
     assert np.abs(jv - fd).max() < 1e-6 * np.abs(jv).max()
+
+
+@pytest.mark.parametrize("dim,p,state", [(2, 2, "vortex"), (3, 2, "density_wave")])
+def test_batched_local_vjp_equals_column_by_column(dim, p, state):
+    """local_vjp_batched (all columns at once on copies of the neighbourhood) equals the
+    column-by-column local_vjp to rounding, also for an element on a periodic face."""
+    from oracle.jacobian import local_vjp_batched
+    D, um = disc(dim, p, state)
+    rng = np.random.default_rng(5)
+    cot = rng.standard_normal(um.shape)
+    for e in (0, D.E - 1):
+        a = local_vjp(D, um, cot, e)
+        b = local_vjp_batched(D, um, cot, e)
+        assert np.abs(a - b).max() < 1e-13 * np.abs(a).max()
+
+
+def test_batched_local_vjp_in_long_double():
+    """In long double (complex long double steps) on a sub-mesh, the batched local VJP agrees
+    with FP64 to FP64 rounding and is itself a transpose to long-double rounding."""
+    from oracle import extended
+    from oracle.jacobian import local_vjp_batched
+    X = np.longdouble
+    if np.finfo(X).eps >= np.finfo(float).eps / 100:
+        pytest.skip("no extended long double")
+    L = 2 * np.pi
+    mesh, Xn = I.config_mesh(2, 3, L, 2, True)
+    D, um = disc(2, 2, "vortex")
+    rng = np.random.default_rng(6)
+    cot = rng.standard_normal(um.shape)
+    e = 7
+    nb = np.unique(np.concatenate([[e], D.geo.nbr_elem[e]]))
+    ring = np.unique(np.concatenate([nb, D.geo.nbr_elem[nb].ravel()]))
+    Dx, need, local = extended.discretization(D, Xn, ring)
+    ie = int(np.searchsorted(need, e))
+    gx = local_vjp_batched(Dx, um[need], cot[need], ie)
+    g64 = local_vjp_batched(D, um, cot, e)
+    assert gx.dtype == X
+    assert np.abs(gx - g64).max() < 1e-12 * np.abs(gx).max()
+    v = rng.standard_normal(um.shape[1:])
+    U = um[need].astype(np.clongdouble)
+    U[ie] += 1j * 1e-30 * v
+    inb = np.searchsorted(need, nb)
+    jv = np.imag(Dx.rhs(U, "sparse", elems=inb)) / 1e-30
+    lhs, rhs = np.sum(gx * v), np.sum(cot[nb].astype(X) * jv)
+    assert abs(lhs - rhs) < 1e3 * np.finfo(X).eps * np.sum(np.abs(gx * v))

@@ -6,6 +6,9 @@ meshes larger than that array before launching anything.
 Collected last on purpose (file name), so a failure here stops a -x run only after every
 other test has run."""
 import ctypes
+import os
+import subprocess
+import sys
 
 import numpy as np
 import pytest
@@ -56,3 +59,38 @@ def test_static_scratch_rejects_meshes_beyond_its_limit():
     assert b"limited to" in E.lib().esd_last_error()
     torch.cuda.synchronize()
     assert float(out.abs().max()) == 0.0     # nothing was launched
+
+
+def test_static_scratch_after_device_reset():
+    """The scratch array's device address is looked up on each call, so the entry point
+    still matches esd_rhs after the process's context has been reset and the library's
+    device code reloaded (run in a child process that uses no torch)."""
+    child = os.path.join(os.path.dirname(os.path.abspath(__file__)), "no_alloc_reset_child.py")
+    r = subprocess.run([sys.executable, child], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stdout + r.stderr
+    lines = [l.split() for l in r.stdout.splitlines() if l.startswith("round")]
+    assert len(lines) == 2, r.stdout
+    for l in lines:
+        assert all(float(e) < 1e-12 for e in l[3:]), l
+
+
+def test_calls_on_another_current_device_are_rejected():
+    """A mesh belongs to the device current at its creation; a compute call made while
+    another device is current returns ESD_ERR_ARG before launching anything.  With one
+    GPU the mismatch is made by overwriting the handle's recorded device (test hook)."""
+    import torch
+    import paper_2312_07874_gb300 as E
+    gm, un = _setup(2, 4, 2, "vortex")
+    u = gm.l2_project(torch.from_numpy(un).cuda())
+    out = torch.zeros_like(u)
+    dev = torch.cuda.current_device()
+    assert E.lib().esd_debug_set_mesh_device(gm.handle, dev + 1) == 0
+    for call in (E.lib().esd_rhs, E.lib().esd_rhs_static_scratch):
+        assert call(gm.handle, E._ptr(u), E._ptr(out), None) == -1
+        assert b"is current" in E.lib().esd_last_error()
+    torch.cuda.synchronize()
+    assert float(out.abs().max()) == 0.0     # nothing was launched
+    assert E.lib().esd_debug_set_mesh_device(gm.handle, dev) == 0
+    assert E.lib().esd_rhs_static_scratch(gm.handle, E._ptr(u), E._ptr(out), None) == 0
+    torch.cuda.synchronize()
+    assert float(out.abs().max()) > 0.0
