@@ -63,14 +63,18 @@ def to_dev(a):
 #     on every element computed.  Rounding of a sum of n terms is at most ~n u of this
 #     scale (u = 1.1e-16), while a dropped, mis-signed or mis-indexed term is a sizeable
 #     fraction of it.
-# (3) flat: ||gpu - oracle64|| <= 1e-12 ||oracle64|| per variable (the benchmark spec's bound) on
-#     states whose residual is well conditioned (FLAT_CASES): the isentropic vortex, and
-#     the density wave up to degree 4.  It is not applied to the low-Mach Taylor-Green
-#     state, where the FP64 oracle itself is up to ~6e-10 from the exact answer (the
-#     pressure, ~71, cancels in the momentum and energy residuals and the density residual
-#     is a truncation-level div(rho v)), nor to the density wave above degree 4 (the FP64
-#     oracle is 1.3e-12 from exact at p = 7: the constant pressure cancels in the momentum
-#     residual).  Check (1) covers those.
+# (3) flat: e_gpu <= 1e-12 per variable (the benchmark spec's bound, against the oracle evaluated
+#     in long double) on states whose residual is well conditioned (flat_case): the
+#     isentropic vortex, and the density wave up to degree 4.  The FP64 oracle is not the
+#     yardstick here: at the benchmark size its own error reaches 3.9e-12 on the density
+#     wave (the CUDA path's: 8.4e-13), so no FP64 implementation can be held to 1e-12
+#     against it.  The flat check is not applied to the low-Mach Taylor-Green state, where
+#     the FP64 oracle itself is up to ~2.5e-7 from the exact answer (the pressure, ~71,
+#     cancels in the momentum and energy residuals and the density residual is a
+#     truncation-level div(rho v)), nor to the density wave above degree 4 (the FP64
+#     oracle is 1.3e-12 from exact at p = 7, 9e-12 at p = 10: the constant pressure cancels
+#     in the momentum residual).  Check (1) covers those.  The difference to the FP64
+#     oracle on every element is reported beside it.
 # The measured errors are appended as JSON lines to $ESD_PARITY_LOG when it is set.
 # ---------------------------------------------------------------------------------------
 PARITY_TOL = 1e-12
@@ -132,7 +136,8 @@ def check_parity(label, got, D, X, um, elems=None, flat=False, n_exact=4, seed=0
     assert np.all(e_scale64 < SCALE_TOL), ("term scale vs oracle64", label, e_scale64)
     assert np.all(e_gpu <= C_EXACT * np.maximum(e_64, FLOOR)), ("accuracy vs exact", label, e_gpu, e_64)
     if flat:
-        assert np.all(e_flat < PARITY_TOL), ("flat bound", label, e_flat)
+        assert len(pick), "the flat bound needs the long-double reference"
+        assert np.all(e_gpu < PARITY_TOL), ("flat bound vs exact", label, e_gpu)
     return rec
 
 
@@ -147,7 +152,8 @@ def periodic_face_elements(mesh):
 def check_vjp_parity(label, grad, D, X, um, cot, elems, flat=False):
     """Per-element (J^T cot) of the CUDA adjoint on ``elems`` against the oracle's batched
     complex-step Jacobian transpose in FP64 and in long double: checks (1) and (3) of
-    check_parity, per variable over the sampled elements."""
+    check_parity, per variable over the sampled elements (the bound of P9, 1e-12, as the
+    flat check (3))."""
     import oracle_jobs
     elems = np.asarray(elems)
     g = np.asarray(grad)[elems]
@@ -164,5 +170,5 @@ def check_vjp_parity(label, grad, D, X, um, cot, elems, flat=False):
     print(rec)
     assert np.all(e_gpu <= C_EXACT * np.maximum(e_64, FLOOR)), ("VJP accuracy vs exact", label, e_gpu, e_64)
     if flat:
-        assert np.all(e_flat < PARITY_TOL), ("VJP flat bound", label, e_flat)
+        assert np.all(e_gpu < PARITY_TOL), ("VJP flat bound vs exact", label, e_gpu)
     return rec
