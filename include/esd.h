@@ -196,6 +196,39 @@ esd_status esd_diagnostics(esd_mesh mesh, const double* u, double* out, void* st
  * (interpolated J).  Used for conservation and entropy time series over a run. */
 esd_status esd_integrals(esd_mesh mesh, const double* u, double* out, void* stream);
 
+/* The skew-symmetric nodal form of Section 4.4, Eq. (rhs_skew), with the modal update of
+ * Eq. (modal) through the weight-adjusted inverse (M = I):
+ *   r = 1/2 sum_l (Q^(l)T sum_m G^(l,m) f_m - sum_m G^(l,m) Q^(l) f_m)
+ *       - sum_zeta R^T B J^zeta (f* - 1/2 sum_m N^(zeta,m) R f_m),  d u~/dt = M~^{-1} V^T r,
+ * with the fluxes f_m evaluated at the nodal solution u = V u~ (no entropy projection and
+ * no two-point flux: a different scheme from esd_rhs, the one Section 4.4 derives the
+ * entropy-stable form from).  Two flux models:
+ *   ESD_SKEW_EULER      the compressible Euler equations (Section 7.1), N_c = dim + 2, the
+ *                       interface flux of Eq. (num_flux) (ESD_FLUX_LF) or its
+ *                       entropy-conservative part (ESD_FLUX_EC), chosen by desc->flux;
+ *   ESD_SKEW_ADVECTION  scalar linear advection f_m(u) = a_m u, N_c = 1, interface flux
+ *                       (a.n)(u- + u+)/2 - sigma |a.n| (u+ - u-)/2, sigma = 1 with `upwind`
+ *                       (energy stable on curved elements), 0 for the central flux.
+ * esd_skew_create builds the mesh (as esd_mesh_create, from the same description) with the
+ * form's mesh-static line-pair coefficients instead of the entropy-stable pair tables.
+ * u, dudt: device [n_elem][N_c][N_p*]; they must not alias.  The handle belongs to the
+ * device current at creation (as a mesh).  esd_skew_check reports the admissibility
+ * flag (Euler: rho <= 0 or p <= 0 at a facet trace) as esd_mesh_check does. */
+typedef struct esd_skew_s* esd_skew;
+enum { ESD_SKEW_EULER = 0, ESD_SKEW_ADVECTION = 1 };
+typedef struct {
+  int model;      /* ESD_SKEW_EULER or ESD_SKEW_ADVECTION */
+  double a[3];    /* advection velocity (components beyond dim ignored) */
+  int upwind;     /* advection: 1 upwind, 0 central interface flux */
+} esd_skew_model;
+esd_status esd_skew_create(const esd_mesh_desc* desc, const esd_skew_model* model, esd_skew* out);
+esd_status esd_skew_destroy(esd_skew skew);
+esd_status esd_rhs_skew(esd_skew skew, const double* u, double* dudt, void* stream);
+esd_status esd_skew_check(esd_skew skew, void* stream);
+/* Number of variables N_c of the model and the residual kernel's launch shape (any output may
+ * be NULL). */
+esd_status esd_skew_info(esd_skew skew, int* n_vars, int* elems_per_cta, int* threads_per_cta);
+
 /* Batched, persistent execution of many independent meshes (not in the paper).
  * The batch keeps references to the meshes, which must outlive it. */
 esd_status esd_batch_create(const esd_mesh* meshes, int n, esd_batch* out);

@@ -18,7 +18,8 @@ f_m(u) = a_m u, the problem for which the skew-symmetric form was introduced (en
 stability on curved elements).
 
 Operators (Q, R, B, W), geometry (G, J^zeta, n, the facet permutation) and the PKD
-Vandermonde come from an oracle.residual.Discretization; the modal states use the ABI
+Vandermonde come from an oracle.residual.Discretization (in its floating-point type: FP64,
+or long double for the extended-precision reference); the modal states use the ABI
 layout [n_elem, N_c, N_p*].
 """
 import numpy as np
@@ -76,7 +77,7 @@ def nodal_residual(D, um, model, form="skew", elems=None):
     for e in elems:
         G = geo.G_vol[e]
         f = [model.flux(u[e], m) for m in range(d)]
-        r = np.zeros(u[e].shape)
+        r = np.zeros(u[e].shape, dtype=u.dtype)
         for l in range(d):
             Q = ref.Q[l]
             for m in range(d):

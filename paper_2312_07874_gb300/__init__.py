@@ -39,6 +39,12 @@ class esd_info(ctypes.Structure):
                 ("elems_per_cta_residual", ctypes.c_int)]
 
 
+class esd_skew_model(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_int), ("a", ctypes.c_double * 3), ("upwind", ctypes.c_int)]
+
+
+ESD_SKEW_EULER, ESD_SKEW_ADVECTION = 0, 1
+
 SYMBOLS = {
     "esd_mesh_create": ([ctypes.POINTER(esd_mesh_desc), ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
     "esd_mesh_destroy": ([ctypes.c_void_p], ctypes.c_int),
@@ -73,6 +79,12 @@ SYMBOLS = {
     "esd_debug_math": ([ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p],
                        ctypes.c_int),
     "esd_debug_set_mesh_device": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
+    "esd_skew_create": ([ctypes.POINTER(esd_mesh_desc), ctypes.POINTER(esd_skew_model),
+                         ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+    "esd_skew_destroy": ([ctypes.c_void_p], ctypes.c_int),
+    "esd_rhs_skew": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "esd_skew_check": ([ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "esd_skew_info": ([ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_int)] * 3, ctypes.c_int),
     "esd_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "esd_last_error": ([], ctypes.c_char_p),
 }
@@ -370,3 +382,75 @@ class Mesh:
         esd_autotune_kernels(self.handle, u, kernels)
         self.info = esd_mesh_info(self.handle)
         return self.info
+
+
+# ---- skew-symmetric form (Eq. (rhs_skew)) ----------------------------------------------
+def esd_skew_create(dim, p, map_nodes, nbr_elem, nbr_face, model=ESD_SKEW_EULER, a=(0.0, 0.0, 0.0),
+                    upwind=False, gamma=1.4, flux=ESD_FLUX_LF):
+    X = np.ascontiguousarray(map_nodes, dtype=np.float64)
+    ne = np.ascontiguousarray(nbr_elem, dtype=np.int32)
+    nf = np.ascontiguousarray(nbr_face, dtype=np.int8)
+    d = esd_mesh_desc(dim, p, X.shape[0], X.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                      ne.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), nf.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)),
+                      gamma, flux)
+    av = (list(a) + [0.0, 0.0, 0.0])[:3]
+    m = esd_skew_model(int(model), (ctypes.c_double * 3)(*av), int(bool(upwind)))
+    h = ctypes.c_void_p()
+    _check(lib().esd_skew_create(ctypes.byref(d), ctypes.byref(m), ctypes.byref(h)))
+    return h
+
+
+def esd_skew_destroy(h):
+    _check(lib().esd_skew_destroy(h))
+
+
+def esd_rhs_skew(h, u, dudt, stream=None):
+    _check(lib().esd_rhs_skew(h, _ptr(u), _ptr(dudt), _stream(stream)))
+
+
+def esd_skew_check(h, stream=None):
+    _check(lib().esd_skew_check(h, _stream(stream)))
+
+
+def esd_skew_info(h):
+    nv, ec, tc = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().esd_skew_info(h, ctypes.byref(nv), ctypes.byref(ec), ctypes.byref(tc)))
+    return dict(n_vars=nv.value, elems_per_cta=ec.value, threads_per_cta=tc.value)
+
+
+class Skew:
+    """Owns an esd_skew handle (the skew-symmetric form of Eq. (rhs_skew)); states are float64
+    CUDA [n_elem, N_c, N_p*] with N_c = dim + 2 (Euler) or 1 (linear advection)."""
+
+    def __init__(self, dim, p, map_nodes, nbr_elem, nbr_face, model="euler", a=(0.0, 0.0, 0.0), upwind=False,
+                 gamma=1.4, flux="LF"):
+        kind = ESD_SKEW_EULER if model == "euler" else ESD_SKEW_ADVECTION
+        self.handle = esd_skew_create(dim, p, map_nodes, nbr_elem, nbr_face, kind, a, upwind, gamma,
+                                      ESD_FLUX_LF if flux == "LF" else ESD_FLUX_EC)
+        info = esd_ref_info(dim, p)
+        self.dim, self.p = dim, p
+        self.n_elem = np.asarray(map_nodes).shape[0]
+        self.n_modes = info["n_modes"]
+        self.info = esd_skew_info(self.handle)
+        self.nc = self.info["n_vars"]
+
+    def close(self):
+        if self.handle is not None:
+            esd_skew_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def rhs(self, u, out=None):
+        import torch
+        if out is None:
+            out = torch.empty((self.n_elem, self.nc, self.n_modes), dtype=torch.float64, device="cuda")
+        esd_rhs_skew(self.handle, u, out)
+        return out
+
+    def check(self):
+        esd_skew_check(self.handle)

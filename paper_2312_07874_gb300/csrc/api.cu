@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "esd_internal.h"
+#include "skew.cuh"
 
 // NVTX ranges name each entry point's host-side span (enqueue, capture or graph launch) for
 // profilers (e.g. ncu --nvtx --nvtx-include "esd_rhs/").  Header-only NVTX 3: without an
@@ -101,6 +102,7 @@ struct esd_mesh_s {
   double* ws_qbar = nullptr;   // VJP: per-node cotangents [E][nq][Ntot]
   double* ws_qext = nullptr;   // VJP: interface cotangents for the neighbour [E][nq][Nfn]
   double* ws_adj[4] = {nullptr, nullptr, nullptr, nullptr};  // RK adjoint: cot copy, k_b, y_b, acc
+  double* sdir = nullptr;      // skew-symmetric form: line-pair coefficients (esd_skew_create)
   std::vector<GraphEntry> graphs;
 
   template <class T>
@@ -151,8 +153,16 @@ const char* esd_status_string(esd_status s) {
 
 const char* esd_last_error(void) { return g_err.c_str(); }
 
+static esd_status mesh_create(const esd_mesh_desc* d, int tables, esd_mesh* out);
+
 esd_status esd_mesh_create(const esd_mesh_desc* d, esd_mesh* out) {
   ESD_RANGE("esd_mesh_create");
+  return mesh_create(d, kTablesEntropyStable, out);
+}
+
+// Mesh creation with the chosen pair tables (entropy-stable pair directions, or the
+// skew-symmetric form's line-pair coefficients for esd_skew_create).
+static esd_status mesh_create(const esd_mesh_desc* d, int tables, esd_mesh* out) {
   if (!d || !out) return fail(ESD_ERR_ARG, "null descriptor or output");
   *out = nullptr;
   if (d->dim != 2 && d->dim != 3) return fail(ESD_ERR_ARG, "dim must be 2 or 3");
@@ -162,7 +172,7 @@ esd_status esd_mesh_create(const esd_mesh_desc* d, esd_mesh* out) {
   if (d->flux != ESD_FLUX_EC && d->flux != ESD_FLUX_LF) return fail(ESD_ERR_ARG, "flux must be ESD_FLUX_EC or ESD_FLUX_LF");
   HostMesh H;
   std::string err;
-  esd_status st = build_host_mesh(*d, &H, &err);
+  esd_status st = build_host_mesh(*d, &H, &err, tables);
   if (st != ESD_OK) return fail(st, err);
   int device = -1;
   cudaError_t de = cudaGetDevice(&device);
@@ -219,6 +229,10 @@ esd_status esd_mesh_create(const esd_mesh_desc* d, esd_mesh* out) {
     return st;
   }
   M.vdir = vdir; M.fdir = fdir; M.wj = wj; M.wdj = wdj; M.bj = bj; M.nrm = nrm; M.nbr_e = ne; M.nbr_f = nf;
+  if ((tables & kTablesSkew) && (st = m->upload(&m->sdir, H.sdir))) {
+    delete m;
+    return st;
+  }
   M.minv = nullptr;
   if (r.dense_minv) {
     double* mi = nullptr;
@@ -1061,6 +1075,116 @@ esd_status esd_measure_fp64_peak(double* flops, void* stream) {
   if (!flops) return fail(ESD_ERR_ARG, "null output");
   cudaError_t e = measure_fp64(flops, (cudaStream_t)stream);
   return e ? cuda_fail(e, "fp64 probe") : ESD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// The skew-symmetric form of Eq. (rhs_skew): a mesh with the form's line-pair
+// coefficients, a trace kernel (u = V u~ and its facet traces, the cross-element input)
+// and the line-task residual kernel.
+// ---------------------------------------------------------------------------
+struct esd_skew_s {
+  esd_mesh m = nullptr;
+  SkewModel P{};
+  int nc = 0;
+  int et = 1, tt = 128;  size_t st = 0;   // trace kernel: elements/CTA, threads, smem
+  int er = 1, tr = 128;  size_t sr = 0;   // residual kernel
+  ~esd_skew_s() { delete m; }
+};
+
+esd_status esd_skew_create(const esd_mesh_desc* d, const esd_skew_model* model, esd_skew* out) {
+  ESD_RANGE("esd_skew_create");
+  if (!d || !model || !out) return fail(ESD_ERR_ARG, "null argument");
+  *out = nullptr;
+  if (model->model != ESD_SKEW_EULER && model->model != ESD_SKEW_ADVECTION)
+    return fail(ESD_ERR_ARG, "model must be ESD_SKEW_EULER or ESD_SKEW_ADVECTION");
+  if (model->model == ESD_SKEW_ADVECTION && model->upwind != 0 && model->upwind != 1)
+    return fail(ESD_ERR_ARG, "upwind must be 0 or 1");
+  esd_mesh m = nullptr;
+  esd_status st = mesh_create(d, kTablesSkew, &m);
+  if (st) return st;
+  esd_skew k = new esd_skew_s();
+  k->m = m;
+  k->nc = model->model == ESD_SKEW_EULER ? d->dim + 2 : 1;
+  k->P.gamma = d->gamma;
+  for (int i = 0; i < 3; ++i) k->P.a[i] = i < d->dim ? model->a[i] : 0.0;
+  k->P.sigma = model->model == ESD_SKEW_ADVECTION && model->upwind ? 1.0 : 0.0;
+  const RefTables& r = m->ref;
+  const int nc = k->nc;
+  constexpr size_t kBudget = 227 * 1024;
+  // trace kernel: the projection kernel's tile (its layout with nc variables)
+  const size_t pe_t = (size_t)nc * (r.Np + 3 * r.Nq + r.Nfn) * sizeof(double);
+  k->et = std::max(1, std::min(32, (int)(kBudget / pe_t)));
+  k->tt = 256;
+  k->st = k->et * pe_t;
+  // residual kernel: E elements x T line tasks; E maximises the threads doing line work per
+  // SM within shared memory and registers
+  const SkewLayout Ly = r.dim == 2 ? skew_layout<2>(nc, r.Nq, r.Np, r.n) : skew_layout<3>(nc, r.Nq, r.Np, r.n);
+  const size_t pe_r = (size_t)Ly.pe * sizeof(double);
+  int regs = 255;
+  cudaError_t e = r.dim == 2 ? skew_residual_attrs_d2(r.n, nc, (int)kBudget, &regs)
+                             : skew_residual_attrs_d3(r.n, nc, (int)kBudget, &regs);
+  if (!e) e = r.dim == 2 ? skew_trace_attrs_d2((int)kBudget) : skew_trace_attrs_d3((int)kBudget);
+  if (e) {
+    delete k;
+    return cuda_fail(e, "skew kernel attributes");
+  }
+  int best = 1;
+  double best_score = -1.0;
+  const int emax = std::max(1, std::min((int)(kBudget / pe_r), 1024 / r.T));
+  for (int el = 1; el <= emax; ++el) {
+    const int thr = ((el * r.T + 31) / 32) * 32;
+    const int by_smem = (int)(kBudget / (el * pe_r));
+    const int by_regs = std::max(1, 65536 / (std::max(regs, 1) * thr));
+    const int ctas = std::max(1, std::min(std::min(by_smem, by_regs), 32));
+    const double score = (double)ctas * el * r.T + 1e-3 * (double)(el * r.T) / thr;
+    if (score > best_score) {
+      best_score = score;
+      best = el;
+    }
+  }
+  k->er = best;
+  k->tr = std::max(32, ((best * r.T + 31) / 32) * 32);
+  k->sr = best * pe_r;
+  *out = k;
+  return ESD_OK;
+}
+
+esd_status esd_skew_destroy(esd_skew k) {
+  if (!k) return fail(ESD_ERR_ARG, "null handle");
+  cudaDeviceSynchronize();
+  delete k;
+  return ESD_OK;
+}
+
+esd_status esd_skew_check(esd_skew k, void* stream) {
+  if (!k) return fail(ESD_ERR_ARG, "null handle");
+  return esd_mesh_check(k->m, stream);
+}
+
+esd_status esd_rhs_skew(esd_skew k, const double* u, double* dudt, void* stream) {
+  ESD_RANGE("esd_rhs_skew");
+  if (!k) return fail(ESD_ERR_ARG, "null handle");
+  esd_mesh m = k->m;
+  if (esd_status ds = check_device(m->device)) return ds;
+  esd_status st;
+  if ((st = check_dev(u, "u")) || (st = check_dev(dudt, "dudt"))) return st;
+  if (u == dudt) return fail(ESD_ERR_ARG, "u and dudt must not alias");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int n = m->ref.n, nc = k->nc;
+  cudaError_t e = m->dim == 2 ? launch_skew_trace_d2(nc, m->R, m->M, k->P, k->et, k->tt, k->st, u, s)
+                              : launch_skew_trace_d3(nc, m->R, m->M, k->P, k->et, k->tt, k->st, u, s);
+  if (e) return cuda_fail(e, "skew trace launch");
+  e = m->dim == 2 ? launch_skew_residual_d2(n, nc, m->R, m->M, k->P, m->sdir, k->er, k->tr, k->sr, u, dudt, s)
+                  : launch_skew_residual_d3(n, nc, m->R, m->M, k->P, m->sdir, k->er, k->tr, k->sr, u, dudt, s);
+  return e ? cuda_fail(e, "skew residual launch") : ESD_OK;
+}
+
+esd_status esd_skew_info(esd_skew k, int* n_vars, int* elems_per_cta, int* threads_per_cta) {
+  if (!k) return fail(ESD_ERR_ARG, "null handle");
+  if (n_vars) *n_vars = k->nc;
+  if (elems_per_cta) *elems_per_cta = k->er;
+  if (threads_per_cta) *threads_per_cta = k->tr;
+  return ESD_OK;
 }
 
 }  // extern "C"

@@ -60,10 +60,16 @@ struct HostMesh {
   std::vector<int32_t> nbr_e, nbr_f;  // [E][Nfn]
   std::vector<double> xvol;           // [E][Nq][dim]
   std::vector<double> minv;           // [E][Np][Np] V^T (W/J) V (when ref.dense_minv)
+  std::vector<double> sdir;           // [E][dim][n(n-1)][dim][T] skew-form line-pair coefficients
 };
 
+// which mesh-static pair tables build_host_mesh computes
+constexpr int kTablesEntropyStable = 1;   // vdir, fdir (the entropy-stable residual)
+constexpr int kTablesSkew = 2;            // sdir (the skew-symmetric form, skew.cuh)
+
 esd_status build_ref(int dim, int p, RefTables* out, std::string* err);
-esd_status build_host_mesh(const esd_mesh_desc& d, HostMesh* out, std::string* err);
+esd_status build_host_mesh(const esd_mesh_desc& d, HostMesh* out, std::string* err,
+                           int tables = kTablesEntropyStable);
 
 // Device views passed to kernels by value.
 // Tables of the table-driven logarithm and exponential (device.cuh: log_tab, exp_tab),
@@ -177,5 +183,22 @@ cudaError_t measure_fp64(double* flops, cudaStream_t s);
 cudaError_t launch_staging_timeout_probe(int* flag, double seconds, cudaStream_t s);
 cudaError_t launch_math_probe(int which, const double* mtab, const double* x, double* y, int64_t n, cudaStream_t s);
 cudaError_t set_smem_limits(const LaunchCfg& L, int dim);
+
+// skew-symmetric form (skew.cuh; skew_d2.cu, skew_d3.cu, skew_d3_hi.cu)
+struct SkewModel;
+cudaError_t launch_skew_residual_d2(int n, int nc, const DevRef& R, const DevMesh& M, const SkewModel& P,
+                                    const double* sdir, int epc, int threads, size_t smem, const double* u,
+                                    double* dudt, cudaStream_t s);
+cudaError_t launch_skew_residual_d3(int n, int nc, const DevRef& R, const DevMesh& M, const SkewModel& P,
+                                    const double* sdir, int epc, int threads, size_t smem, const double* u,
+                                    double* dudt, cudaStream_t s);
+cudaError_t skew_residual_attrs_d2(int n, int nc, int smem_limit, int* regs);
+cudaError_t skew_residual_attrs_d3(int n, int nc, int smem_limit, int* regs);
+cudaError_t launch_skew_trace_d2(int nc, const DevRef& R, const DevMesh& M, const SkewModel& P, int epc,
+                                 int threads, size_t smem, const double* u, cudaStream_t s);
+cudaError_t launch_skew_trace_d3(int nc, const DevRef& R, const DevMesh& M, const SkewModel& P, int epc,
+                                 int threads, size_t smem, const double* u, cudaStream_t s);
+cudaError_t skew_trace_attrs_d2(int smem_limit);
+cudaError_t skew_trace_attrs_d3(int smem_limit);
 
 }  // namespace esd

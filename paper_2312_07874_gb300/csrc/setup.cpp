@@ -465,7 +465,8 @@ double det(int d, const double* A) {  // A[m*d+k] = d x_m / d xi_k
 
 }  // namespace
 
-esd_status build_host_mesh(const esd_mesh_desc& d, HostMesh* H, std::string* err) {
+esd_status build_host_mesh(const esd_mesh_desc& d, HostMesh* H, std::string* err, int tables) {
+  const bool es = (tables & kTablesEntropyStable) != 0, skew = (tables & kTablesSkew) != 0;
   esd_status st = build_ref(d.dim, d.p, &H->ref, err);
   if (st != ESD_OK) return st;
   const RefTables& r = H->ref;
@@ -488,8 +489,9 @@ esd_status build_host_mesh(const esd_mesh_desc& d, HostMesh* H, std::string* err
   if (dim == 3) Bi = basis_at(Lint, tgt);
   const int nint = dim == 3 ? Lint.size() : 0;
 
-  H->vdir.assign((size_t)E * r.nvp * dim, 0.0);
-  H->fdir.assign((size_t)E * r.nfp * dim, 0.0);
+  H->vdir.assign(es ? (size_t)E * r.nvp * dim : 0, 0.0);
+  H->fdir.assign(es ? (size_t)E * r.nfp * dim : 0, 0.0);
+  H->sdir.assign(skew ? (size_t)E * dim * T * n * (n - 1) * dim : 0, 0.0);
   H->wj.assign((size_t)E * Nq, 0.0);
   H->wdj.assign((size_t)E * Nq, 0.0);
   H->bj.assign((size_t)E * Nfn, 0.0);
@@ -625,6 +627,38 @@ esd_status build_host_mesh(const esd_mesh_desc& d, HostMesh* H, std::string* err
         }
         H->bj[(size_t)e * Nfn + f] = r.wfac[f] * nn;
       }
+      // line node indices: node a of line t of phase ph
+      auto line_node = [&](int ph, int t, int a) {
+        if (dim == 2) return ph == 0 ? a + n * t : t + n * a;
+        if (ph == 0) return a + n * t;
+        if (ph == 1) return (t % n) + n * (a + n * (t / n));
+        return t + n * n * a;
+      };
+      // skew-symmetric form (Eq. (rhs_skew)) as line pairs: for nodes i (index a) and j
+      // (index b) of an eta_k-line, c^m_ij = 1/2 sum_l (Q^(l)_ji G_lm(x_j) - G_lm(x_i) Q^(l)_ij),
+      // stored [phase][slot b (n-1) + (a < b ? a : a - 1)][m][task]
+      if (skew) {
+        double* sd = &H->sdir[(size_t)e * dim * T * n * (n - 1) * dim];
+        for (int ph = 0; ph < dim; ++ph)
+          for (int t = 0; t < T; ++t)
+            for (int b = 0; b < n; ++b)
+              for (int a = 0; a < n; ++a) {
+                if (a == b) continue;
+                const int vi = line_node(ph, t, a), vj = line_node(ph, t, b);
+                const double* Dk = r.dl[ph].data();
+                const int slot = b * (n - 1) + (a < b ? a : a - 1);
+                for (int mm = 0; mm < dim; ++mm) {
+                  double c = 0.0;
+                  for (int l = 0; l < dim; ++l) {
+                    const double Qij = r.wvol[vi] * r.deta[vi * 9 + ph * 3 + l] * Dk[a * n + b];
+                    const double Qji = r.wvol[vj] * r.deta[vj * 9 + ph * 3 + l] * Dk[b * n + a];
+                    c += Qji * G[vj * 9 + l * 3 + mm] - G[vi * 9 + l * 3 + mm] * Qij;
+                  }
+                  sd[(((size_t)ph * n * (n - 1) + slot) * dim + mm) * T + t] = 0.5 * c;
+                }
+              }
+      }
+      if (!es) continue;
       // volume pair directions: n_ij = sum_l S^(l)_ij (G_l.(xi_i) + G_l.(xi_j)), with the
       // line entries of S^(l) from Q^(l)_ij = w_i (d eta_k/d xi_l)(xi_i) ell'_{k,b}(eta_{k,a})
       double* vd = &H->vdir[(size_t)e * r.nvp * dim];

@@ -63,28 +63,23 @@ def to_dev(a):
 #     on every element computed.  Rounding of a sum of n terms is at most ~n u of this
 #     scale (u = 1.1e-16), while a dropped, mis-signed or mis-indexed term is a sizeable
 #     fraction of it.
-# (3) flat: e_gpu <= 1e-12 per variable (the benchmark spec's bound, against the oracle evaluated
-#     in long double) on states whose residual is well conditioned (flat_case): the
-#     isentropic vortex, and the density wave up to degree 4.  The FP64 oracle is not the
-#     yardstick here: at the benchmark size its own error reaches 3.9e-12 on the density
-#     wave (the CUDA path's: 8.4e-13), so no FP64 implementation can be held to 1e-12
-#     against it.  The flat check is not applied to the low-Mach Taylor-Green state, where
-#     the FP64 oracle itself is up to ~2.5e-7 from the exact answer (the pressure, ~71,
-#     cancels in the momentum and energy residuals and the density residual is a
-#     truncation-level div(rho v)), nor to the density wave above degree 4 (the FP64
-#     oracle is 1.3e-12 from exact at p = 7, 9e-12 at p = 10: the constant pressure cancels
-#     in the momentum residual).  Check (1) covers those.  The difference to the FP64
-#     oracle on every element is reported beside it.
+# (3) flat: the benchmark spec's 1e-12 relative max-norm per variable, against the oracle
+#     evaluated in long double, for every variable where an FP64 evaluation of the method
+#     can meet it: where the FP64 oracle's own error e_64 is below half of it (FLAT_REACH).
+#     The FP64 oracle is not the yardstick itself: at the benchmark size its error on the
+#     density wave is 3.9e-12 (the CUDA path's: 8.4e-13), on the low-Mach Taylor-Green
+#     state up to 1.2e-5 in density at p = 6 (the pressure, ~71, cancels in the momentum
+#     and energy residuals and the density residual is a truncation-level div(rho v)), and
+#     on the noisy vortex at p = 10 5.4e-11; there no FP64 implementation can be held to
+#     1e-12 and check (1) is the bound.  The difference to the FP64 oracle on every element
+#     is reported beside it.
 # The measured errors are appended as JSON lines to $ESD_PARITY_LOG when it is set.
 # ---------------------------------------------------------------------------------------
 PARITY_TOL = 1e-12
+FLAT_REACH = 0.5e-12
 C_EXACT = 10.0
 FLOOR = 4 * 2.0 ** -53
 SCALE_TOL = 1e-12
-
-
-def flat_case(state, p):
-    return state == "vortex" or (state == "density_wave" and p <= 4)
 
 
 def scale_err_per_var(got, ref, scale):
@@ -102,7 +97,7 @@ def _log(record):
             f.write(json.dumps(record) + "\n")
 
 
-def check_parity(label, got, D, X, um, elems=None, flat=False, n_exact=4, seed=0, oracle=None):
+def check_parity(label, got, D, X, um, elems=None, n_exact=4, seed=0, oracle=None):
     """Apply checks (1)-(3) to the CUDA path's d u~/dt ``got`` of the elements ``elems``
     (all when None); ``oracle`` = (d u~/dt, term scale) of the FP64 oracle for those
     elements if already computed.  The long-double reference runs on ``n_exact`` of them
@@ -126,18 +121,17 @@ def check_parity(label, got, D, X, um, elems=None, flat=False, n_exact=4, seed=0
         e_scale = scale_err_per_var(got[pick], rx, sx)
     else:                  # no long-double reference requested: checks (2) vs FP64 and (3) only
         e_gpu = e_64 = e_scale = np.zeros(got.shape[1])
+    flat = (e_64 < FLAT_REACH) if len(pick) else np.zeros(len(e_64), bool)
     rec = dict(case=label, e_gpu_exact=e_gpu.tolist(), e_oracle64_exact=e_64.tolist(),
                e_gpu_oracle64=e_flat.tolist(), e_term_scale=e_scale.tolist(),
-               e_term_scale_oracle64=e_scale64.tolist(), flat=bool(flat), n_elems=int(len(elems)),
+               e_term_scale_oracle64=e_scale64.tolist(), flat=flat.tolist(), n_elems=int(len(elems)),
                n_exact=int(len(pick)))
     _log(rec)
     print(rec)
     assert np.all(e_scale < SCALE_TOL), ("term scale vs exact", label, e_scale)
     assert np.all(e_scale64 < SCALE_TOL), ("term scale vs oracle64", label, e_scale64)
     assert np.all(e_gpu <= C_EXACT * np.maximum(e_64, FLOOR)), ("accuracy vs exact", label, e_gpu, e_64)
-    if flat:
-        assert len(pick), "the flat bound needs the long-double reference"
-        assert np.all(e_gpu < PARITY_TOL), ("flat bound vs exact", label, e_gpu)
+    assert np.all(e_gpu[flat] < PARITY_TOL), ("flat bound vs exact", label, e_gpu, e_64)
     return rec
 
 
@@ -149,7 +143,7 @@ def periodic_face_elements(mesh):
     return np.nonzero((d > mesh.L / 2).any(axis=(1, 2)))[0]
 
 
-def check_vjp_parity(label, grad, D, X, um, cot, elems, flat=False):
+def check_vjp_parity(label, grad, D, X, um, cot, elems):
     """Per-element (J^T cot) of the CUDA adjoint on ``elems`` against the oracle's batched
     complex-step Jacobian transpose in FP64 and in long double: checks (1) and (3) of
     check_parity, per variable over the sampled elements (the bound of P9, 1e-12, as the
@@ -164,11 +158,11 @@ def check_vjp_parity(label, grad, D, X, um, cot, elems, flat=False):
     e_gpu = np.asarray(rel_err_per_var(g, gx), dtype=float)
     e_64 = np.asarray(rel_err_per_var(g64, gx), dtype=float)
     e_flat = np.asarray(rel_err_per_var(g, g64), dtype=float)
+    flat = e_64 < FLAT_REACH
     rec = dict(case=label, e_gpu_exact=e_gpu.tolist(), e_oracle64_exact=e_64.tolist(),
-               e_gpu_oracle64=e_flat.tolist(), flat=bool(flat), n_elems=int(len(elems)))
+               e_gpu_oracle64=e_flat.tolist(), flat=flat.tolist(), n_elems=int(len(elems)))
     _log(rec)
     print(rec)
     assert np.all(e_gpu <= C_EXACT * np.maximum(e_64, FLOOR)), ("VJP accuracy vs exact", label, e_gpu, e_64)
-    if flat:
-        assert np.all(e_gpu < PARITY_TOL), ("VJP flat bound vs exact", label, e_gpu)
+    assert np.all(e_gpu[flat] < PARITY_TOL), ("VJP flat bound vs exact", label, e_gpu, e_64)
     return rec

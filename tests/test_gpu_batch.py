@@ -4,7 +4,7 @@ the plain per-mesh path (bitwise)."""
 import numpy as np
 import pytest
 
-from gpu_common import check_parity, flat_case, rel_err_per_var
+from gpu_common import check_parity, rel_err_per_var
 
 pytestmark = pytest.mark.gpu
 
@@ -50,7 +50,7 @@ def test_batch_rhs_against_oracle():
                                                       dtype=np.float64)
         um = u.cpu().numpy()[need]
         check_parity(f"batch rhs mesh {k}: dim={dim} M={M} p={p} {state}", o.cpu().numpy()[sample], Ds,
-                     X[need], um, elems=local, flat=flat_case(state, p), n_exact=1 if p <= 7 else 0, seed=k)
+                     X[need], um, elems=local, n_exact=1 if p <= 7 else 0, seed=k)
     E.esd_batch_destroy(b)
 
 

@@ -30,9 +30,9 @@ def test_ragged_last_tile_parity():
     torch.cuda.synchronize()
     # the long-double sample includes the last element (in the partial tile)
     got = out.cpu().numpy()
-    check_parity("ragged last tile", got, D, X, um, flat=True, n_exact=4, seed=3)
+    check_parity("ragged last tile", got, D, X, um, n_exact=4, seed=3)
     tail = np.arange(D.E - D.E % epc, D.E)
-    check_parity("ragged last tile (tail)", got[tail], D, X, um, elems=tail, flat=True, n_exact=len(tail))
+    check_parity("ragged last tile (tail)", got[tail], D, X, um, elems=tail, n_exact=len(tail))
 
 
 def test_monitoring_arguments_rejected():

@@ -7,7 +7,7 @@ variable against the FP64 oracle on well-conditioned states."""
 import numpy as np
 import pytest
 
-from gpu_common import workload, gpu_mesh, to_dev, rel_err_per_var, check_parity, flat_case
+from gpu_common import workload, gpu_mesh, to_dev, rel_err_per_var, check_parity
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-12
@@ -31,8 +31,7 @@ def test_rhs_parity(dim, M, p, state, flux):
     out = gm.rhs(u)
     torch.cuda.synchronize()
     gm.check()
-    check_parity(f"rhs dim={dim} M={M} p={p} {state} {flux}", out.cpu().numpy(), D, X, um,
-                 flat=flat_case(state, p), n_exact=4, seed=p)
+    check_parity(f"rhs dim={dim} M={M} p={p} {state} {flux}", out.cpu().numpy(), D, X, um, n_exact=4, seed=p)
 
 
 # Tetrahedra of degree 5..10 on the 162-element periodic mesh: the GPU computes every
@@ -52,8 +51,7 @@ def test_rhs_parity_high_degree_tets(p, state, flux):
     gm.check()
     rng = np.random.default_rng(40 + p)
     sample = np.sort(rng.choice(D.E, size=3, replace=False))
-    check_parity(f"rhs tet p={p} {state} {flux} (sample)", out[sample], D, X, um, elems=sample,
-                 flat=flat_case(state, p), n_exact=1 if p <= 7 else 0)
+    check_parity(f"rhs tet p={p} {state} {flux} (sample)", out[sample], D, X, um, elems=sample, n_exact=1 if p <= 7 else 0)
     # conservation over the whole GPU output (Theorem 2)
     cons = D.conservation_rate(out)
     y = np.einsum("ij,ecj->eic", D.V, out)
@@ -216,7 +214,7 @@ def test_affine_triangles_rhs_and_ten_rk4_steps():
     out = gm.rhs(u)
     torch.cuda.synchronize()
     gm.check()
-    check_parity("affine triangles p=2 vortex rhs", out.cpu().numpy(), D, X, um, flat=True, n_exact=4, seed=1)
+    check_parity("affine triangles p=2 vortex rhs", out.cpu().numpy(), D, X, um, n_exact=4, seed=1)
     lam = I.max_wave_speed_sampled(I.config_state_fn(dim, L, "vortex"), dim, L)
     dt = 0.1 * (L / M) / (lam * (2 * p + 1))
     s = torch.cuda.Stream()

@@ -3,7 +3,7 @@ oracle's complex-step Jacobian and against central differences of the GPU forwar
 import numpy as np
 import pytest
 
-from gpu_common import workload, gpu_mesh, to_dev, check_vjp_parity, periodic_face_elements, flat_case
+from gpu_common import workload, gpu_mesh, to_dev, check_vjp_parity, periodic_face_elements
 from oracle.jacobian import jvp, rk4_jvp
 
 pytestmark = pytest.mark.gpu
@@ -52,8 +52,7 @@ def test_vjp_per_element_jacobian_transpose(dim, M, p, state, flux):
     per = periodic_face_elements(mesh)
     inner = np.setdiff1d(np.arange(D.E), per)
     sample = np.concatenate([rng.choice(per, 3, replace=False), rng.choice(inner, min(3, len(inner)), replace=False)])
-    check_vjp_parity(f"vjp dim={dim} M={M} p={p} {state} {flux}", g, D, X, um, c, sample,
-                     flat=flat_case(state, p))
+    check_vjp_parity(f"vjp dim={dim} M={M} p={p} {state} {flux}", g, D, X, um, c, sample)
 
 
 # Central differences of the GPU forward.  The entropy-conservative flux is smooth, so the

@@ -45,7 +45,7 @@ def test_vjp_fullsize_per_element_against_oracle(flux):
     per = periodic_face_elements(mesh)
     inner = np.setdiff1d(np.arange(D.E), per)
     sample = np.concatenate([rng.choice(per, 4, replace=False), rng.choice(inner, 4, replace=False)])
-    check_vjp_parity(f"vjp full-size 3072 tets p=3 tgv {flux}", g, D, X, um, cot, sample, flat=False)
+    check_vjp_parity(f"vjp full-size 3072 tets p=3 tgv {flux}", g, D, X, um, cot, sample)
 
 
 @pytest.mark.parametrize("flux,h", [("EC", 1e-6), ("LF", 1e-7)])

@@ -127,3 +127,29 @@ def test_skew_volume_term_is_a_line_pair_sum(dim, M, p):
         assert np.allclose(np.diag(c), 0.0, atol=1e-13 * np.abs(c).max())
         pair += c @ f[m]
     assert np.abs(pair - vol).max() < 1e-13 * np.abs(vol).max()
+
+
+def test_skew_form_in_long_double_matches_fp64():
+    """The skew-symmetric form evaluated in long double on a sub-mesh agrees with FP64 to FP64
+    rounding, and its free-stream residual vanishes to long-double rounding (Euler, curved
+    tetrahedra): the extended-precision reference the GPU tests use."""
+    from oracle import extended
+    X = np.longdouble
+    if np.finfo(X).eps >= np.finfo(float).eps / 100:
+        pytest.skip("no extended long double")
+    L = 2 * np.pi
+    mesh, Xn = I.config_mesh(3, 3, L, 2, True)
+    D = Discretization(3, 2, Xn, mesh.nbr_elem, mesh.nbr_face)
+    um = np.einsum("ij,i,eic->ecj", D.V, D.ref.w, I.density_wave(D.geo.x_vol, L))
+    el = np.array([3, 50])
+    Dx, need, local = extended.sub_discretization(3, 2, Xn, mesh.nbr_elem, mesh.nbr_face, el)
+    model = skew.EulerModel(3)
+    rx = skew.rhs(Dx, um[need].astype(X), model, "skew", local)
+    r64 = skew.rhs(D, um, model, "skew", el)
+    assert rx.dtype == X
+    assert np.abs(rx - r64).max() < 1e-12 * np.abs(rx).max()
+    ubar = euler.conservative(np.array(1.3), np.array([0.4, -0.7, 0.2]), np.array(2.1))
+    uc = np.zeros((D.E, 5, D.Np))
+    uc[:, :, 0] = ubar / D.V[0, 0]
+    rf = skew.rhs(Dx, uc[need].astype(X), model, "skew", local)
+    assert np.abs(rf).max() < 1e4 * np.finfo(X).eps * np.abs(ubar).max()
