@@ -89,6 +89,32 @@ def residual_kernel_flops(D, p):
             + NC * (lift + dudt) + reduce4), vol_pairs + fac_pairs + Nfn
 
 
+def skew_node_flux_flops(D, nc):
+    """f_m(u) at one node: Euler (reciprocal with two Newton steps, v, p, the D flux
+    vectors), or a_m u for linear advection."""
+    if nc == 1:
+        return D
+    return 9 + 3 * D + 4 + D * (1 + 2 * D + 1)
+
+
+def skew_residual_flops(D, p, nc):
+    """Per element, the skew-symmetric residual kernel (Eq. (rhs_skew)): u = V u~, the line
+    pairs (one FMA per ordered pair, direction and variable), the node fluxes formed in each
+    phase and for the facet traces, the facet terms and lifts, d u~/dt = [V^T (W/J) V] V^T r."""
+    n = p + 1
+    V, VT, Nq, Np = transform_fmas(D, p)
+    T = n ** (D - 1)
+    pairs = 2 * D * T * n * (n - 1) * D * nc
+    flux_evals = D * Nq + (3 * T * n if D == 3 else 3 * n * n) + (T * n if D == 3 else 0)
+    fluxes = flux_evals * skew_node_flux_flops(D, nc)
+    traces = 2 * D * nc * ((3 * T * n) + (2 * T * n if D == 3 else 0))
+    Nfn = (D + 1) * n ** (D - 1)
+    fstar = Nfn * ((interface_flops(D) if nc > 1 else 12) + 2 * D * nc + 2 * nc)
+    lift = 2 * nc * ((3 * T * n) + (2 * T * n if D == 3 else 0))
+    dudt = 2 * nc * (V + VT + V + VT) + nc * Nq
+    return pairs + fluxes + traces + fstar + lift + dudt
+
+
 def project_kernel_flops(D, p):
     n = p + 1
     NC = D + 2
@@ -698,6 +724,53 @@ def run_sweep(args):
                       "l2": "flushed (256 MB write) before every timed call", "dtype": "f64"}), flush=True)
 
 
+def run_skew(args):
+    """The skew-symmetric form (esd_rhs_skew, Eq. (rhs_skew)) against the entropy-stable
+    esd_rhs on the same meshes and states: 24576 curved tetrahedra (TGV) and 8192 curved
+    triangles (vortex) at p = 4, Euler with LF facets, and linear advection (upwind) of the
+    density.  One line per workload; L2 flushed before every timed call."""
+    import torch
+    import paper_2312_07874_gb300 as E
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(32 * 1024 * 1024, dtype=torch.float64, device=dev)
+    peak = E.esd_measure_fp64_peak(stream)
+    reps = max(3, args.steps)
+    for name, dim, M, L, p, state in [("tet_tgv_curved", 3, 16, 2 * np.pi, 4, "tgv"),
+                                      ("tri_vortex_curved", 2, 64, 1.0, 4, "vortex")]:
+        mesh, X = I.config_mesh(dim, M, L, p, True)
+        gm = E.Mesh(dim, p, X, mesh.nbr_elem, mesh.nbr_face, flux="LF")
+        x = gm.volume_nodes()
+        f = I.config_state_fn(dim, L, state)
+        u = gm.l2_project(torch.from_numpy(np.ascontiguousarray(np.transpose(f(x), (0, 2, 1)))).to(dev))
+        gm.autotune(u, E.ESD_TUNE_PROJECT | E.ESD_TUNE_RESIDUAL)
+        out = torch.empty_like(u)
+        es_ms = _time_flushed(torch, stream, lambda: E.esd_rhs(gm.handle, u, out, stream), reps, flush)
+        nE = gm.info["n_elem"]
+        line = {"kind": "skew", "workload": f"{name} p={p} ({nE} elements)", "esd_rhs_ms": es_ms}
+        for model in ("euler", "advection"):
+            sk = E.Skew(dim, p, X, mesh.nbr_elem, mesh.nbr_face, model=model, a=(1.0, 0.6, -0.35)[:dim],
+                        upwind=True, flux="LF")
+            us = u if model == "euler" else u[:, :1].contiguous()
+            so = torch.empty_like(us)
+            ms = _time_flushed(torch, stream, lambda: E.esd_rhs_skew(sk.handle, us, so, stream), reps, flush)
+            sk.check()
+            nc = sk.nc
+            dof = nE * gm.n_modes * nc
+            fl = skew_residual_flops(dim, p, nc)
+            line[model] = {"esd_rhs_skew_ms": ms, "dof_residual_updates_per_s": dof / (ms * 1e-3),
+                           "skew_residual_flops_per_elem": fl,
+                           "whole_call_tflops": fl * nE / (ms * 1e-3) / 1e12,
+                           "whole_call_frac_of_measured_fp64": fl * nE / (ms * 1e-3) / peak,
+                           "launch": sk.info}
+            del sk, us, so
+        line.update({"fp64_peak_tflops": peak / 1e12, "l2": "flushed (256 MB write) before every timed call",
+                     "dtype": "f64"})
+        print(json.dumps(line), flush=True)
+        del gm, u, out
+        torch.cuda.empty_cache()
+
+
 def run_diagnostics_series(args):
     """Conservation and entropy over a run: Taylor-Green vortex at Mach 0.1 on 4^3 x 6 = 384
     curved tetrahedra, p = 4, entropy-conservative (EC) and Lax-Friedrichs (LF) interface
@@ -743,6 +816,8 @@ def main():
     ap.add_argument("--batch-small", action="store_true", help="with --batch: 64 small meshes instead")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes (profiling)")
     ap.add_argument("--diagnostics", action="store_true", help="conservation / entropy time series (EC and LF)")
+    ap.add_argument("--skew", action="store_true", help="the skew-symmetric form (esd_rhs_skew) against "
+                    "esd_rhs on the tetrahedron and triangle workloads at p = 4")
     ap.add_argument("--sweep", action="store_true", help="per-degree throughput of the triangle and "
                     "tetrahedron workloads and the differentiation workload (one line each)")
     args = ap.parse_args()
@@ -755,6 +830,9 @@ def main():
         return
     if args.diagnostics:
         run_diagnostics_series(args)
+        return
+    if args.skew:
+        run_skew(args)
         return
     if args.warmup < 3:
         args.warmup = 3

@@ -1131,10 +1131,12 @@ esd_status esd_skew_create(const esd_mesh_desc* d, const esd_skew_model* model, 
   int best = 1;
   double best_score = -1.0;
   const int emax = std::max(1, std::min((int)(kBudget / pe_r), 1024 / r.T));
+  const int regs_alloc = (std::max(regs, 1) + 7) / 8 * 8;   // registers are allocated in groups of 8
   for (int el = 1; el <= emax; ++el) {
     const int thr = ((el * r.T + 31) / 32) * 32;
+    if (el > 1 && (size_t)thr * regs_alloc > 65536) break;   // the block must fit the register file
     const int by_smem = (int)(kBudget / (el * pe_r));
-    const int by_regs = std::max(1, 65536 / (std::max(regs, 1) * thr));
+    const int by_regs = std::max(1, 65536 / (regs_alloc * thr));
     const int ctas = std::max(1, std::min(std::min(by_smem, by_regs), 32));
     const double score = (double)ctas * el * r.T + 1e-3 * (double)(el * r.T) / thr;
     if (score > best_score) {
