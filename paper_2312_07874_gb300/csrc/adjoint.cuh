@@ -265,22 +265,17 @@ __device__ void apply_RT(const DevRef& R, const Tile& t, int in, int y, int out,
 // and facet nodes (qbar [E][NQ][Ntot]) and, per facet node, the cotangent of the
 // neighbour's state through this element's interface flux (qext [E][NQ][Nfn]).
 struct AdjLayout {
-  int oReg, oM, oS1, oS2, oSv, oSf, oIp, oRb, oHb, oQv, oQf, oPart, pe;
+  int oReg, oM, oS1, oS2, oSv, oSf, oIp, oRb, oHb, oQv, oQf, pe;
   int glob;   // 1: q_b accumulated in the global output instead of shared memory
-  int ncol;   // facet-4 columns per pass of the partial sums
   // oIp: 1/p of every node ([Nq + Nfn] after the states), or -1 where it does not fit
   // (then computed per pair)
 };
 
 // Shared memory per element of the residual adjoint.  The per-node cotangents q_b are
 // accumulated in shared memory when everything fits in one CTA's 227 KB; otherwise
-// (tetrahedra of degree >= 9) they are accumulated in place in the global output q_b
-// (`glob`), and the facet-4 partials run in passes of facet4_cols(n) columns.
+// (tetrahedra of the highest degrees) they are accumulated in place in the global output
+// q_b (`glob`).
 constexpr int kAdjSmemBudget = 227 * 1024;
-
-// Facet-4 columns per pass of the adjoint's facet-4 partial sums: all n of them, or half
-// at n = 11 where the full set would not fit next to the states.
-__host__ __device__ constexpr int facet4_cols(int n) { return n > 10 ? (n + 1) / 2 : n; }
 
 template <int D>
 __host__ __device__ inline AdjLayout adj_layout_with(int Nq, int Nfn, int Np, int n, bool glob, bool ip) {
@@ -302,14 +297,12 @@ __host__ __device__ inline AdjLayout adj_layout_with(int Nq, int Nfn, int Np, in
   if (!glob) {
     L.oQv = L.oHb + NC * Nfn;
     L.oQf = L.oQv + NQ * Nq;
-    L.oPart = L.oQf + NQ * Nfn;
-    L.ncol = n;
+    L.pe = L.oQf + NQ * Nfn;
   } else {
     L.oQv = L.oQf = -1;
-    L.oPart = L.oHb + NC * Nfn;
-    L.ncol = facet4_cols(n);
+    L.pe = L.oHb + NC * Nfn;
   }
-  L.pe = L.oPart + (D == 3 ? NQ * n * n * L.ncol : 0);
+  (void)n;
   return L;
 }
 

@@ -1120,9 +1120,9 @@ esd_status esd_skew_create(const esd_mesh_desc* d, const esd_skew_model* model, 
   // SM within shared memory and registers
   const SkewLayout Ly = r.dim == 2 ? skew_layout<2>(nc, r.Nq, r.Np, r.n) : skew_layout<3>(nc, r.Nq, r.Np, r.n);
   const size_t pe_r = (size_t)Ly.pe * sizeof(double);
-  int regs = 255;
-  cudaError_t e = r.dim == 2 ? skew_residual_attrs_d2(r.n, nc, (int)kBudget, &regs)
-                             : skew_residual_attrs_d3(r.n, nc, (int)kBudget, &regs);
+  int regs = 255, max_thr = 256;
+  cudaError_t e = r.dim == 2 ? skew_residual_attrs_d2(r.n, nc, (int)kBudget, &regs, &max_thr)
+                             : skew_residual_attrs_d3(r.n, nc, (int)kBudget, &regs, &max_thr);
   if (!e) e = r.dim == 2 ? skew_trace_attrs_d2((int)kBudget) : skew_trace_attrs_d3((int)kBudget);
   if (e) {
     delete k;
@@ -1134,7 +1134,7 @@ esd_status esd_skew_create(const esd_mesh_desc* d, const esd_skew_model* model, 
   const int regs_alloc = (std::max(regs, 1) + 7) / 8 * 8;   // registers are allocated in groups of 8
   for (int el = 1; el <= emax; ++el) {
     const int thr = ((el * r.T + 31) / 32) * 32;
-    if (el > 1 && (size_t)thr * regs_alloc > 65536) break;   // the block must fit the register file
+    if (el > 1 && (thr > max_thr || (size_t)thr * regs_alloc > 65536)) break;   // the block must fit
     const int by_smem = (int)(kBudget / (el * pe_r));
     const int by_regs = std::max(1, 65536 / (regs_alloc * thr));
     const int ctas = std::max(1, std::min(std::min(by_smem, by_regs), 32));

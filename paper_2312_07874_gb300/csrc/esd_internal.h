@@ -192,8 +192,8 @@ cudaError_t launch_skew_residual_d2(int n, int nc, const DevRef& R, const DevMes
 cudaError_t launch_skew_residual_d3(int n, int nc, const DevRef& R, const DevMesh& M, const SkewModel& P,
                                     const double* sdir, int epc, int threads, size_t smem, const double* u,
                                     double* dudt, cudaStream_t s);
-cudaError_t skew_residual_attrs_d2(int n, int nc, int smem_limit, int* regs);
-cudaError_t skew_residual_attrs_d3(int n, int nc, int smem_limit, int* regs);
+cudaError_t skew_residual_attrs_d2(int n, int nc, int smem_limit, int* regs, int* max_threads);
+cudaError_t skew_residual_attrs_d3(int n, int nc, int smem_limit, int* regs, int* max_threads);
 cudaError_t launch_skew_trace_d2(int nc, const DevRef& R, const DevMesh& M, const SkewModel& P, int epc,
                                  int threads, size_t smem, const double* u, cudaStream_t s);
 cudaError_t launch_skew_trace_d3(int nc, const DevRef& R, const DevMesh& M, const SkewModel& P, int epc,

@@ -247,24 +247,31 @@ __global__ void residual_adjoint_kernel(DevRef R, DevMesh M, int epc, const doub
       for (int a = 0; a < n; ++a) {
         const int vi = base + a * stride;
         NodeState<D> Si = load_state<D>(Sv, Nq, vi);
+        const double ipi = ip_v(Si, vi);
+        // node a's cotangent accumulates in registers over its pairs (one shared-memory
+        // update per node instead of a read-modify-write chain through every pair)
+        double qa[NQ], rbi[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          qa[c] = 0.0;
+          rbi[c] = rb[c * Nq + vi];
+        }
         for (int b = a + 1; b < n; ++b, ++m) {
           const int vj = base + b * stride;
           NodeState<D> Sj = load_state<D>(Sv, Nq, vj);
-          double nn[D], Fb[NC], qa[NQ], qb[NQ];
+          double nn[D], Fb[NC], qb[NQ];
           load_dir<D>(vdir, ph * R.Lv + m, T, t, nn);
 #pragma unroll
           for (int c = 0; c < NC; ++c) {
-            Fb[c] = rb[c * Nq + vj] - rb[c * Nq + vi];
-            qa[c] = 0.0;
+            Fb[c] = rb[c * Nq + vj] - rbi[c];
             qb[c] = 0.0;
           }
-          ec_flux_adj<D>(Si, Sj, nn, inv_gm1, Fb, qa, qb, ip_v(Si, vi), ip_v(Sj, vj));
+          ec_flux_adj<D>(Si, Sj, nn, inv_gm1, Fb, qa, qb, ipi, ip_v(Sj, vj));
 #pragma unroll
-          for (int c = 0; c < NQ; ++c) {
-            qv[c * qvs + vi] += qa[c];
-            qv[c * qvs + vj] += qb[c];
-          }
+          for (int c = 0; c < NQ; ++c) qv[c * qvs + vj] += qb[c];
         }
+#pragma unroll
+        for (int c = 0; c < NQ; ++c) qv[c * qvs + vi] += qa[c];
       }
       auto facet_pairs = [&](const double* fd, int slot0, int f, int cnt) {
         NodeState<D> Sfj = load_state<D>(Sf, Nfn, f);
@@ -298,30 +305,34 @@ __global__ void residual_adjoint_kernel(DevRef R, DevMesh M, int epc, const doub
     }
     __syncthreads();
   }
-  // facet 4, in passes over the facet-4 columns b' (all of them in one pass unless the
-  // partials do not fit)
-  for (int b0 = 0; D == 3 && b0 < n; b0 += Ly.ncol) {
-    const int b1 = b0 + Ly.ncol < n ? b0 + Ly.ncol : n, NB = Ly.ncol;
-    double* part = sm + el * pe + Ly.oPart;
-    if (active) {
-      const int a = t % n, b2 = t / n;
-      const double* fd = fdir + R.fph_off[3];
-      for (int bp = b0; bp < b1; ++bp) {
-        int m = bp * n;
+  // facet 4 on the forward's diagonal schedule: task (a, b2) owns the volume nodes
+  // (a, b2, .); in step k it handles facet-4 node (a, b') with b' = (b2 + k) mod n, whose
+  // cotangent only it updates in that step (the tasks sharing a hold distinct b'), so no
+  // partial sums are kept; a barrier separates the steps.
+  if (D == 3) {
+    const int a = t % n, b2 = t / n;
+    const double* fd = active ? fdir + R.fph_off[3] : nullptr;
+#pragma unroll 1
+    for (int k = 0; k < n; ++k) {
+      if (active) {
+        const int bp = b2 + k < n ? b2 + k : b2 + k - n;
         const int f = 3 * Nqf + a + n * bp;
         NodeState<D> Sfj = load_state<D>(Sf, Nfn, f);
         const double ipj = ip_f(Sfj, f);
-        double acc[NQ];
+        double acc[NQ], hbf[NC];
 #pragma unroll
-        for (int c = 0; c < NQ; ++c) acc[c] = 0.0;
-        for (int b3 = 0; b3 < n; ++b3, ++m) {
+        for (int c = 0; c < NC; ++c) {
+          acc[c] = 0.0;
+          hbf[c] = hb[c * Nfn + f];
+        }
+        for (int b3 = 0; b3 < n; ++b3) {
           const int vi = a + n * (b2 + n * b3);
           NodeState<D> Si = load_state<D>(Sv, Nq, vi);
           double nn[D], Fb[NC], qa[NQ];
-          load_dir<D>(fd, m, T, t, nn);
+          load_dir<D>(fd, bp * n + b3, T, t, nn);
 #pragma unroll
           for (int c = 0; c < NC; ++c) {
-            Fb[c] = -rb[c * Nq + vi] - hb[c * Nfn + f];
+            Fb[c] = -rb[c * Nq + vi] - hbf[c];
             qa[c] = 0.0;
           }
           ec_flux_adj<D>(Si, Sfj, nn, inv_gm1, Fb, qa, acc, ip_v(Si, vi), ipj);
@@ -329,20 +340,10 @@ __global__ void residual_adjoint_kernel(DevRef R, DevMesh M, int epc, const doub
           for (int c = 0; c < NQ; ++c) qv[c * qvs + vi] += qa[c];
         }
 #pragma unroll
-        for (int c = 0; c < NQ; ++c) part[(c * T + t) * NB + (bp - b0)] = acc[c];
+        for (int c = 0; c < NQ; ++c) qf[c * qfs + f] += acc[c];
       }
+      __syncthreads();
     }
-    __syncthreads();
-    const int nb = b1 - b0;
-    for (int idx = threadIdx.x; idx < E * NQ * n * nb; idx += blockDim.x) {
-      int e = idx / (NQ * n * nb), rr = idx % (NQ * n * nb), c = rr / (n * nb), j = rr % (n * nb);
-      int a = j % n, bq = j / n;
-      const double* pp = sm + e * pe + Ly.oPart + c * T * NB;
-      double s = 0.0;
-      for (int b2 = 0; b2 < n; ++b2) s += pp[(a + n * b2) * NB + bq];
-      qf_of(e)[c * qfs + 3 * Nqf + a + n * (b0 + bq)] += s;
-    }
-    __syncthreads();
   }
   // 6. store q cotangents (already in place when accumulated in global memory)
   if (Ly.glob) return;
@@ -595,9 +596,8 @@ bool audit_layouts(std::string* err) {
       if (states_end > A.oRb || (A.oIp >= 0 && A.oIp < states_end) ||
           (A.oIp >= 0 && A.oIp + r.Nq + r.Nfn > A.oRb) || A.oM + NC * r.Np > A.oRb)
         return bad(dim, p, "adjoint states / scratch");
-      if (A.oHb + NC * r.Nfn > (A.glob ? A.oPart : A.oQv)) return bad(dim, p, "adjoint h_b");
-      if (!A.glob && (A.oQf + NQ * r.Nfn > A.oPart)) return bad(dim, p, "adjoint q_b");
-      if (A.oPart + (dim == 3 ? NQ * r.T * A.ncol : 0) > A.pe) return bad(dim, p, "adjoint partials");
+      if (A.oHb + NC * r.Nfn > (A.glob ? A.pe : A.oQv)) return bad(dim, p, "adjoint h_b");
+      if (!A.glob && (A.oQf + NQ * r.Nfn > A.pe)) return bad(dim, p, "adjoint q_b");
       if (C.tv > 512 || C.tv < C.ev * r.T) return bad(dim, p, "adjoint threads");
     }
   }

@@ -17,9 +17,9 @@ cudaError_t launch_skew_residual_d2(int n, int nc, const DevRef& R, const DevMes
 #undef X
 }
 
-cudaError_t skew_residual_attrs_d2(int n, int nc, int smem_limit, int* regs) {
+cudaError_t skew_residual_attrs_d2(int n, int nc, int smem_limit, int* regs, int* max_threads) {
 #define X(N) \
-  case N: return nc == 1 ? skew_residual_attrs_n<2, N, 1>(smem_limit, regs) : skew_residual_attrs_n<2, N, 4>(smem_limit, regs);
+  case N: return nc == 1 ? skew_residual_attrs_n<2, N, 1>(smem_limit, regs, max_threads) : skew_residual_attrs_n<2, N, 4>(smem_limit, regs, max_threads);
   switch (n) { ESD_SKEW_CASES(X) default: return cudaErrorInvalidValue; }
 #undef X
 }

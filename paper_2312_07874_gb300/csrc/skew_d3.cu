@@ -7,7 +7,7 @@ namespace esd {
 cudaError_t launch_skew_residual_d3_hi(int n, int nc, const DevRef& R, const DevMesh& M, const SkewModel& P,
                                        const double* sdir, int epc, int threads, size_t smem, const double* u,
                                        double* dudt, cudaStream_t s);
-cudaError_t skew_residual_attrs_d3_hi(int n, int nc, int smem_limit, int* regs);
+cudaError_t skew_residual_attrs_d3_hi(int n, int nc, int smem_limit, int* regs, int* max_threads);
 
 #define ESD_SKEW_CASES(X) X(2) X(3) X(4) X(5) X(6) X(7)
 
@@ -25,10 +25,10 @@ cudaError_t launch_skew_residual_d3(int n, int nc, const DevRef& R, const DevMes
 #undef X
 }
 
-cudaError_t skew_residual_attrs_d3(int n, int nc, int smem_limit, int* regs) {
+cudaError_t skew_residual_attrs_d3(int n, int nc, int smem_limit, int* regs, int* max_threads) {
 #define X(N) \
-  case N: return nc == 1 ? skew_residual_attrs_n<3, N, 1>(smem_limit, regs) : skew_residual_attrs_n<3, N, 5>(smem_limit, regs);
-  switch (n) { ESD_SKEW_CASES(X) default: return skew_residual_attrs_d3_hi(n, nc, smem_limit, regs); }
+  case N: return nc == 1 ? skew_residual_attrs_n<3, N, 1>(smem_limit, regs, max_threads) : skew_residual_attrs_n<3, N, 5>(smem_limit, regs, max_threads);
+  switch (n) { ESD_SKEW_CASES(X) default: return skew_residual_attrs_d3_hi(n, nc, smem_limit, regs, max_threads); }
 #undef X
 }
 

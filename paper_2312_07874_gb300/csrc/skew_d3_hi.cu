@@ -16,9 +16,9 @@ cudaError_t launch_skew_residual_d3_hi(int n, int nc, const DevRef& R, const Dev
 #undef X
 }
 
-cudaError_t skew_residual_attrs_d3_hi(int n, int nc, int smem_limit, int* regs) {
+cudaError_t skew_residual_attrs_d3_hi(int n, int nc, int smem_limit, int* regs, int* max_threads) {
 #define X(N) \
-  case N: return nc == 1 ? skew_residual_attrs_n<3, N, 1>(smem_limit, regs) : skew_residual_attrs_n<3, N, 5>(smem_limit, regs);
+  case N: return nc == 1 ? skew_residual_attrs_n<3, N, 1>(smem_limit, regs, max_threads) : skew_residual_attrs_n<3, N, 5>(smem_limit, regs, max_threads);
   switch (n) { ESD_SKEW_CASES(X) default: return cudaErrorInvalidValue; }
 #undef X
 }

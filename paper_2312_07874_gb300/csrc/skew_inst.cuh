@@ -16,14 +16,19 @@ cudaError_t launch_skew_residual_n(const DevRef& R, const DevMesh& M, const Skew
   return cudaGetLastError();
 }
 
+// Sets the kernel's dynamic shared-memory limit and reports its registers per thread and
+// the largest block the runtime accepts for it (registers included).
 template <int D, int N, int NC>
-cudaError_t skew_residual_attrs_n(int smem_limit, int* regs) {
+cudaError_t skew_residual_attrs_n(int smem_limit, int* regs, int* max_threads) {
   cudaError_t e = cudaFuncSetAttribute(skew_residual_kernel<D, N, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        smem_limit);
   if (e) return e;
   cudaFuncAttributes a;
   e = cudaFuncGetAttributes(&a, skew_residual_kernel<D, N, NC>);
-  if (!e) *regs = a.numRegs;
+  if (!e) {
+    *regs = a.numRegs;
+    *max_threads = a.maxThreadsPerBlock;
+  }
   return e;
 }
 
