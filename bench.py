@@ -607,7 +607,23 @@ def run_batch(args):
 
     ms_batch = timed(lambda: E.esd_batch_rk_step(b, ua, dts, stream))
     ms_plain = timed(lambda: [m.rk_step(u, dt) for m, u, dt in zip(meshes, ub, dts)])
+    # where the per-mesh path's time goes: each mesh's RK4 step alone (its graph), and the
+    # share of the meshes too small to fill the GPU (fewer residual CTAs than two per SM),
+    # the only time that batching can recover
+    per_mesh = [timed(lambda m=m, u=u, dt=dt: m.rk_step(u, dt)) for m, u, dt in zip(meshes, ub, dts)]
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    small = [i for i, m in enumerate(meshes)
+             if (m.n_elem + m.info["elems_per_cta_residual"] - 1) // m.info["elems_per_cta_residual"] < 2 * sms]
+    small_ms = sum(per_mesh[i] for i in small)
+    order = sorted(range(len(meshes)), key=lambda i: -per_mesh[i])
     line = {"metric": "FP64 DOF-residual updates/s, 64-mesh batch (RK4 steps)", "unit": UNIT,
+            "per_mesh_breakdown": {
+                "sum_of_single_mesh_steps_ms": sum(per_mesh),
+                "largest_8": [{"mesh": f"{'tri' if mix[i][0] == 2 else 'tet'} M={mix[i][1]} p={mix[i][2]}",
+                               "n_elem": meshes[i].n_elem, "ms": per_mesh[i]} for i in order[:8]],
+                "share_of_largest_8": sum(per_mesh[i] for i in order[:8]) / sum(per_mesh),
+                "meshes_under_two_ctas_per_sm": len(small), "their_ms": small_ms,
+                "speedup_bound_if_their_time_vanished": sum(per_mesh) / max(sum(per_mesh) - small_ms, 1e-9)},
             "batched": {"value": 4.0 * dof / (ms_batch * 1e-3), "ms_per_step": ms_batch,
                         "launches_per_step": None},
             "plain_per_mesh": {"value": 4.0 * dof / (ms_plain * 1e-3), "ms_per_step": ms_plain,

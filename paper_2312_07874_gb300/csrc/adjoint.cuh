@@ -265,8 +265,11 @@ __device__ void apply_RT(const DevRef& R, const Tile& t, int in, int y, int out,
 // and facet nodes (qbar [E][NQ][Ntot]) and, per facet node, the cotangent of the
 // neighbour's state through this element's interface flux (qext [E][NQ][Nfn]).
 struct AdjLayout {
-  int oReg, oM, oS1, oS2, oSv, oSf, oIp, oRb, oHb, oQv, oQf, pe;
+  int oReg, oM, oS1, oS2, oSv, oSf, oIp, oRb, oHb, oQv, oQf, oQvx, oQf4x, pe;
   int glob;   // 1: q_b accumulated in the global output instead of shared memory
+  int conc;   // 1: the D line families run concurrently, families 1.. into their own
+              //    volume-node cotangent copies at oQvx and (tetrahedra) facet-4 node
+              //    cotangent copies at oQf4x, summed in a fixed order after
   // oIp: 1/p of every node ([Nq + Nfn] after the states), or -1 where it does not fit
   // (then computed per pair)
 };
@@ -278,7 +281,8 @@ struct AdjLayout {
 constexpr int kAdjSmemBudget = 227 * 1024;
 
 template <int D>
-__host__ __device__ inline AdjLayout adj_layout_with(int Nq, int Nfn, int Np, int n, bool glob, bool ip) {
+__host__ __device__ inline AdjLayout adj_layout_with(int Nq, int Nfn, int Np, int n, bool glob, bool ip,
+                                                     bool conc) {
   constexpr int NC = D + 2, NF = D + 5, NQ = D + 2;
   AdjLayout L;
   L.oReg = 0;
@@ -294,27 +298,50 @@ __host__ __device__ inline AdjLayout adj_layout_with(int Nq, int Nfn, int Np, in
   L.oRb = r0;
   L.oHb = L.oRb + NC * Nq;
   L.glob = glob ? 1 : 0;
+  L.conc = (!glob && conc) ? 1 : 0;
+  L.oQvx = L.oQf4x = -1;
   if (!glob) {
     L.oQv = L.oHb + NC * Nfn;
     L.oQf = L.oQv + NQ * Nq;
     L.pe = L.oQf + NQ * Nfn;
+    if (L.conc) {
+      L.oQvx = L.pe;
+      L.pe += (D - 1) * NQ * Nq;
+      if (D == 3) {
+        L.oQf4x = L.pe;
+        L.pe += (D - 1) * NQ * n * n;
+      }
+    }
   } else {
     L.oQv = L.oQf = -1;
     L.pe = L.oHb + NC * Nfn;
   }
-  (void)n;
   return L;
 }
 
-// the first of (q_b in shared memory, with 1/p), (without 1/p), (q_b in global memory,
-// with 1/p), (without) that fits in one CTA
+// Threads of a residual-adjoint CTA of e elements: the e*T line tasks of one family,
+// rounded up to whole warps, times D when the families run concurrently (family-major, so
+// that no warp mixes two families' code paths).
+template <int D>
+__host__ __device__ inline int adj_block_threads(const AdjLayout& L, int T, int e) {
+  const int per_family = ((e * T + 31) / 32) * 32;
+  return L.conc ? D * per_family : per_family;
+}
+
+// The first layout that fits one CTA (and, for concurrent families, leaves room for at least
+// two elements per SM): q_b in shared memory with concurrent families and 1/p, then without
+// 1/p, then sequential families with and without 1/p, then q_b in global memory.
 template <int D>
 __host__ __device__ inline AdjLayout adj_layout(int Nq, int Nfn, int Np, int n) {
-  for (int k = 0; k < 4; ++k) {
-    const AdjLayout L = adj_layout_with<D>(Nq, Nfn, Np, n, k >= 2, (k & 1) == 0);
-    if ((long long)L.pe * 8 <= kAdjSmemBudget || k == 3) return L;
+  const bool glob[6] = {false, false, false, false, true, true};
+  const bool ip[6] = {true, false, true, false, true, false};
+  const bool conc[6] = {true, true, false, false, false, false};
+  for (int k = 0; k < 6; ++k) {
+    const AdjLayout L = adj_layout_with<D>(Nq, Nfn, Np, n, glob[k], ip[k], conc[k]);
+    const long long lim = conc[k] ? kAdjSmemBudget / 2 : kAdjSmemBudget;
+    if ((long long)L.pe * 8 <= lim) return L;
   }
-  return adj_layout_with<D>(Nq, Nfn, Np, n, true, false);
+  return adj_layout_with<D>(Nq, Nfn, Np, n, true, false, false);
 }
 
 }  // namespace esd

@@ -958,11 +958,12 @@ esd_status esd_autotune_kernels(esd_mesh m, const double* u, int kernels, void* 
   // residual adjoint (esd_rhs_vjp): elements per CTA
   if (kernels & ESD_TUNE_ADJOINT) {
     float tbest = 1e30f;
-    const int emax = std::min(std::max(1, (int)(budget / smem_residual_adj(r, 1))), std::max(1, 1024 / r.T));
+    const int emax = std::max(1, (int)(budget / smem_residual_adj(r, 1)));
     for (int e = 1; e <= emax; ++e) {
+      if (e > 1 && adj_threads_host(r, e) > 512) break;   // 128 registers per thread
       LaunchCfg L = best;
       L.ev = e;
-      L.tv = std::max(64, ((e * r.T + 31) / 32) * 32);
+      L.tv = std::max(64, adj_threads_host(r, e));
       L.sv = smem_residual_adj(r, e);
       float t = time_launches([&] {
         return launch_vjp(m->R, m->M, L, u, m->ws_adj[0], m->ws_adj[1], m->ws_qbar, m->ws_qext, s);

@@ -144,6 +144,7 @@ bool audit_layouts(std::string* err);   // kernels.cu, host only
 size_t smem_project(const RefTables& r, int e);
 size_t smem_residual(const RefTables& r, int e);
 size_t smem_residual_adj(const RefTables& r, int e);
+int adj_threads_host(const RefTables& r, int e);   // threads of a residual-adjoint CTA of e elements
 
 // Kernel launchers (kernels.cu).  All return cudaGetLastError().
 cudaError_t launch_project(const DevRef& R, const DevMesh& M, const LaunchCfg& L, const double* u,

@@ -187,6 +187,13 @@ __global__ void residual_adjoint_kernel(DevRef R, DevMesh M, int epc, const doub
     else
       sm[e * pe + Ly.oQv + idx % (NQ * Ntot)] = 0.0;   // qv and qf are contiguous
   }
+  if (Ly.conc) {   // the families' copies (volume nodes, facet-4 nodes) are contiguous
+    const int nx = (D - 1) * NQ * (Nq + (D == 3 ? n * n : 0));
+    for (int idx = threadIdx.x; idx < E * nx; idx += blockDim.x) {
+      const int e = idx / nx;
+      sm[e * pe + Ly.oQvx + idx % nx] = 0.0;
+    }
+  }
   __syncthreads();
   // 4. interface flux adjoint: f*_b = B J h_b
   for (int idx = threadIdx.x; idx < E * Nfn; idx += blockDim.x) {
@@ -215,10 +222,15 @@ __global__ void residual_adjoint_kernel(DevRef R, DevMesh M, int epc, const doub
     }
   }
   __syncthreads();
-  // 5. pair adjoints, same task structure as the forward phases
+  // 5. pair adjoints, same task structure as the forward phases.  With `conc` the D line
+  //    families run at once (D x T tasks per element), family k > 0 adding its volume-node
+  //    cotangents to its own copy; the copies are summed in a fixed order afterwards, so the
+  //    result does not depend on timing.  Facet nodes of faces 1-3 belong to one family each.
   const int tid = threadIdx.x;
-  const int el = tid / T, t = tid % T;
-  const bool active = el < E;
+  const int tpf = ((epc * T + 31) / 32) * 32;   // threads per family (whole warps)
+  const int fam = Ly.conc ? tid / tpf : 0, rem = Ly.conc ? tid % tpf : tid;
+  const int el = rem / T, t = rem % T;
+  const bool active = el < E && fam < D;
   const int64_t eg = e0 + el;
   const double* vdir = active ? M.vdir + eg * (int64_t)R.nvp * D : nullptr;
   const double* fdir = active ? M.fdir + eg * (int64_t)R.nfp * D : nullptr;
@@ -226,13 +238,14 @@ __global__ void residual_adjoint_kernel(DevRef R, DevMesh M, int epc, const doub
   const double* Sf = sm + el * pe + Ly.oSf;
   const double* rb = sm + el * pe + Ly.oRb;
   const double* hb = sm + el * pe + Ly.oHb;
-  double* qv = active ? qv_of(el) : nullptr;
+  double* qv = !active ? nullptr : (fam > 0 ? sm + el * pe + Ly.oQvx + (fam - 1) * NQ * Nq : qv_of(el));
   double* qf = active ? qf_of(el) : nullptr;
   const double* ipn = sm + el * pe + (Ly.oIp >= 0 ? Ly.oIp : 0);   // [Nq volume | Nfn facet]
   const bool have_ip = Ly.oIp >= 0;
   auto ip_v = [&](const NodeState<D>& S, int v) { return have_ip ? ipn[v] : rcp_nr<2>(S.p); };
   auto ip_f = [&](const NodeState<D>& S, int f) { return have_ip ? ipn[Nq + f] : rcp_nr<2>(S.p); };
-  for (int ph = 0; ph < D; ++ph) {
+  const int ph_begin = Ly.conc ? fam : 0, ph_end = Ly.conc ? fam + 1 : D;
+  for (int ph = ph_begin; ph < ph_end; ++ph) {
     if (active) {
       int base, stride;
       if (D == 2) {
@@ -303,18 +316,26 @@ __global__ void residual_adjoint_kernel(DevRef R, DevMesh M, int epc, const doub
         facet_pairs(fdir + R.fph_off[1], 0, t, n);
       }
     }
-    __syncthreads();
+    if (!Ly.conc) __syncthreads();
   }
+  if (Ly.conc) __syncthreads();
   // facet 4 on the forward's diagonal schedule: task (a, b2) owns the volume nodes
   // (a, b2, .); in step k it handles facet-4 node (a, b') with b' = (b2 + k) mod n, whose
   // cotangent only it updates in that step (the tasks sharing a hold distinct b'), so no
-  // partial sums are kept; a barrier separates the steps.
+  // partial sums are kept; a barrier separates the steps.  With concurrent families the
+  // volume nodes (a, b2, b3) of a task are split by b3 among the families (b3 = fam,
+  // fam + D, ...), each adding its facet-node sums to its own copy.
   if (D == 3) {
     const int a = t % n, b2 = t / n;
-    const double* fd = active ? fdir + R.fph_off[3] : nullptr;
+    const bool act4 = active;
+    double* qv4 = qv;
+    double* qf4 = !act4 ? nullptr : (fam > 0 ? sm + el * pe + Ly.oQf4x + (fam - 1) * NQ * n * n : qf + 3 * Nqf);
+    const int qf4s = fam > 0 ? n * n : qfs;
+    const int b3_0 = Ly.conc ? fam : 0, b3_step = Ly.conc ? D : 1;
+    const double* fd = act4 ? fdir + R.fph_off[3] : nullptr;
 #pragma unroll 1
     for (int k = 0; k < n; ++k) {
-      if (active) {
+      if (act4) {
         const int bp = b2 + k < n ? b2 + k : b2 + k - n;
         const int f = 3 * Nqf + a + n * bp;
         NodeState<D> Sfj = load_state<D>(Sf, Nfn, f);
@@ -325,7 +346,7 @@ __global__ void residual_adjoint_kernel(DevRef R, DevMesh M, int epc, const doub
           acc[c] = 0.0;
           hbf[c] = hb[c * Nfn + f];
         }
-        for (int b3 = 0; b3 < n; ++b3) {
+        for (int b3 = b3_0; b3 < n; b3 += b3_step) {
           const int vi = a + n * (b2 + n * b3);
           NodeState<D> Si = load_state<D>(Sv, Nq, vi);
           double nn[D], Fb[NC], qa[NQ];
@@ -337,13 +358,37 @@ __global__ void residual_adjoint_kernel(DevRef R, DevMesh M, int epc, const doub
           }
           ec_flux_adj<D>(Si, Sfj, nn, inv_gm1, Fb, qa, acc, ip_v(Si, vi), ipj);
 #pragma unroll
-          for (int c = 0; c < NQ; ++c) qv[c * qvs + vi] += qa[c];
+          for (int c = 0; c < NQ; ++c) qv4[c * qvs + vi] += qa[c];
         }
 #pragma unroll
-        for (int c = 0; c < NQ; ++c) qf[c * qfs + f] += acc[c];
+        for (int c = 0; c < NQ; ++c) qf4[c * qf4s + (f - 3 * Nqf)] += acc[c];
       }
       __syncthreads();
     }
+  }
+  if (Ly.conc) {   // sum the families' copies in a fixed order
+    const int nv = NQ * Nq, nf4 = D == 3 ? NQ * n * n : 0;
+    for (int idx = threadIdx.x; idx < E * (nv + nf4); idx += blockDim.x) {
+      const int e = idx / (nv + nf4), r = idx % (nv + nf4);
+      double* dst;
+      const double* src;
+      int str;
+      if (r < nv) {
+        dst = sm + e * pe + Ly.oQv + r;
+        src = sm + e * pe + Ly.oQvx + r;
+        str = nv;
+      } else {
+        const int c = (r - nv) / (n * n), j = (r - nv) % (n * n);
+        dst = sm + e * pe + Ly.oQf + c * Nfn + 3 * Nqf + j;
+        src = sm + e * pe + Ly.oQf4x + (r - nv);
+        str = nf4;
+      }
+      double v = *dst;
+#pragma unroll
+      for (int k = 0; k < D - 1; ++k) v += src[k * str];
+      *dst = v;
+    }
+    __syncthreads();
   }
   // 6. store q cotangents (already in place when accumulated in global memory)
   if (Ly.glob) return;
@@ -505,6 +550,7 @@ size_t smem_residual(const RefTables& r, int e) {
 
 static constexpr size_t kSmemBudget = 227 * 1024;   // opt-in maximum per CTA
 size_t smem_residual_adj(const RefTables& r, int e);
+int adj_threads_host(const RefTables& r, int e);
 
 LaunchCfg choose_launch(const RefTables& r) {
   LaunchCfg L;
@@ -543,20 +589,21 @@ LaunchCfg choose_launch(const RefTables& r) {
   // residual adjoint: same task structure, larger shared footprint
   // (the adjoint kernel uses up to 128 registers per thread: at most 512 threads per block)
   int evmax = std::max(1, (int)(kSmemBudget / smem_residual_adj(r, 1)));
-  evmax = std::min(evmax, std::max(1, 512 / r.T));
   best = 1;
   best_score = -1.0;
   for (int e = 1; e <= evmax; ++e) {
-    int thr = ((e * r.T + 31) / 32) * 32;
-    double util = (double)(e * r.T) / thr;
-    double score = util * std::min(1.0, thr / 128.0) + 1e-3 * e;
+    const int thr = adj_threads_host(r, e);
+    if (thr > 512) break;
+    const double util = (double)(e * r.T) / ((e * r.T + 31) / 32 * 32);
+    const int ctas = std::max(1, std::min((int)(kSmemBudget / smem_residual_adj(r, e)), 2048 / thr));
+    const double score = util * std::min(1.0, ctas * thr / 384.0) + 1e-3 * e;
     if (score > best_score) {
       best_score = score;
       best = e;
     }
   }
   L.ev = best;
-  L.tv = std::max(64, ((best * r.T + 31) / 32) * 32);
+  L.tv = std::max(64, adj_threads_host(r, best));
   L.sv = smem_residual_adj(r, best);
   return L;
 }
@@ -598,7 +645,7 @@ bool audit_layouts(std::string* err) {
         return bad(dim, p, "adjoint states / scratch");
       if (A.oHb + NC * r.Nfn > (A.glob ? A.pe : A.oQv)) return bad(dim, p, "adjoint h_b");
       if (!A.glob && (A.oQf + NQ * r.Nfn > A.pe)) return bad(dim, p, "adjoint q_b");
-      if (C.tv > 512 || C.tv < C.ev * r.T) return bad(dim, p, "adjoint threads");
+      if (C.tv > 512 || C.tv < adj_threads_host(r, C.ev)) return bad(dim, p, "adjoint threads");
     }
   }
   return true;
@@ -666,6 +713,11 @@ cudaError_t launch_l2_project(const DevRef& R, const DevMesh& M, const double* u
   else
     l2_project_kernel<3><<<grid, 256, pe * epc, s>>>(R, M, epc, un, um);
   return cudaGetLastError();
+}
+
+int adj_threads_host(const RefTables& r, int e) {
+  if (r.dim == 2) return adj_block_threads<2>(adj_layout<2>(r.Nq, r.Nfn, r.Np, r.n), r.T, e);
+  return adj_block_threads<3>(adj_layout<3>(r.Nq, r.Nfn, r.Np, r.n), r.T, e);
 }
 
 size_t smem_residual_adj(const RefTables& r, int e) {
