@@ -787,6 +787,65 @@ def run_skew(args):
         torch.cuda.empty_cache()
 
 
+def otf_direction_flops(D, p):
+    """Extra flops per element of forming the pair directions on the fly: per volume pair the
+    D coefficients (Q_ij - Q_ji)/4 (FMA + MUL each) and D^2 (ADD + FMA); per facet pair
+    D (D FMA + MUL) -- the arithmetic the stored tables replace by 3 loads."""
+    n = p + 1
+    vol_pairs = D * n ** (D - 1) * (p * (p + 1) // 2)
+    fac_pairs = 3 * n * n if D == 2 else 3 * n ** 3 + n ** 4
+    return vol_pairs * (3 * D + 3 * D * D) + fac_pairs * D * (2 * D + 1)
+
+
+def run_directions(args):
+    """The pair-direction trade measured both ways: the residual kernel with the stored
+    per-element pair tables (ESD_MESH_PAIR_TABLES) and with directions formed on the fly from
+    per-node metric terms (ESD_MESH_METRICS_ON_THE_FLY), on the same mesh and state; device
+    memory of each mesh, kernel time (L2 flushed), fraction of the measured FP64 peak."""
+    import torch
+    import paper_2312_07874_gb300 as E
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(32 * 1024 * 1024, dtype=torch.float64, device=dev)
+    peak = E.esd_measure_fp64_peak(stream)
+    reps = max(3, args.steps)
+    cases = [("tet_tgv_curved", 3, 16, 2 * np.pi, 4, "tgv"), ("tet_tgv_curved_8", 3, 8, 2 * np.pi, 10, "tgv"),
+             ("tet_tgv_curved", 3, 16, 2 * np.pi, 10, "tgv"), ("tri_vortex_curved", 2, 64, 1.0, 4, "vortex"),
+             ("tri_vortex_curved", 2, 64, 1.0, 10, "vortex")]
+    for name, dim, M, L, p, state in cases:
+        mesh, X = I.config_mesh(dim, M, L, p, True)
+        f = I.config_state_fn(dim, L, state)
+        line = {"kind": "pair_directions", "workload": f"{name} p={p}"}
+        outs = {}
+        for tag, otf in (("stored_pair_tables", False), ("metrics_on_the_fly", True)):
+            gm = E.Mesh(dim, p, X, mesh.nbr_elem, mesh.nbr_face, flux="LF", metrics_on_the_fly=otf)
+            x = gm.volume_nodes()
+            u = gm.l2_project(torch.from_numpy(np.ascontiguousarray(np.transpose(f(x), (0, 2, 1)))).to(dev))
+            gm.autotune(u, E.ESD_TUNE_PROJECT | E.ESD_TUNE_RESIDUAL)
+            out = torch.empty_like(u)
+            E.esd_launch_stage(gm.handle, 0, u, None, stream)
+            ms = _time_flushed(torch, stream, lambda: E.esd_launch_stage(gm.handle, 1, None, out, stream), reps, flush)
+            gm.check()
+            nE = gm.info["n_elem"]
+            fl, _ = residual_kernel_flops(dim, p)
+            extra = otf_direction_flops(dim, p) if otf else 0
+            outs[tag] = out.cpu().numpy()
+            line[tag] = {"residual_kernel_ms": ms, "device_bytes_per_elem": gm.info["device_bytes"] / nE,
+                         "frac_of_measured_fp64": fl * nE / (ms * 1e-3) / peak,
+                         "frac_incl_direction_flops": (fl + extra) * nE / (ms * 1e-3) / peak,
+                         "elems_per_cta": gm.info["elems_per_cta_residual"]}
+            line["n_elem"] = nE
+            del gm, u, out
+            torch.cuda.empty_cache()
+        a, b = outs["stored_pair_tables"], outs["metrics_on_the_fly"]
+        line["max_rel_difference"] = float((np.abs(a - b).max(axis=(0, 2)) / np.abs(a).max(axis=(0, 2))).max())
+        line["time_ratio_otf_over_stored"] = (line["metrics_on_the_fly"]["residual_kernel_ms"]
+                                              / line["stored_pair_tables"]["residual_kernel_ms"])
+        line.update({"fp64_peak_tflops": peak / 1e12, "l2": "flushed (256 MB write) before every timed launch",
+                     "dtype": "f64"})
+        print(json.dumps(line), flush=True)
+
+
 def run_diagnostics_series(args):
     """Conservation and entropy over a run: Taylor-Green vortex at Mach 0.1 on 4^3 x 6 = 384
     curved tetrahedra, p = 4, entropy-conservative (EC) and Lax-Friedrichs (LF) interface
@@ -832,6 +891,8 @@ def main():
     ap.add_argument("--batch-small", action="store_true", help="with --batch: 64 small meshes instead")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes (profiling)")
     ap.add_argument("--diagnostics", action="store_true", help="conservation / entropy time series (EC and LF)")
+    ap.add_argument("--directions", action="store_true", help="the residual kernel with stored pair tables "
+                    "against pair directions formed on the fly from per-node metric terms")
     ap.add_argument("--skew", action="store_true", help="the skew-symmetric form (esd_rhs_skew) against "
                     "esd_rhs on the tetrahedron and triangle workloads at p = 4")
     ap.add_argument("--sweep", action="store_true", help="per-degree throughput of the triangle and "
@@ -849,6 +910,9 @@ def main():
         return
     if args.skew:
         run_skew(args)
+        return
+    if args.directions:
+        run_directions(args)
         return
     if args.warmup < 3:
         args.warmup = 3

@@ -107,6 +107,21 @@ typedef struct {
  * everything and allocates the workspace.  Synchronous.  Errors: ESD_ERR_ARG,
  * ESD_ERR_MESH, ESD_ERR_UNSUPPORTED, ESD_ERR_NOMEM, ESD_ERR_CUDA. */
 esd_status esd_mesh_create(const esd_mesh_desc* desc, esd_mesh* out);
+
+/* esd_mesh_create with a choice of how the flux-differencing kernel obtains its pair
+ * directions (not in the paper's text, a storage/arithmetic trade of Section 5):
+ *   ESD_MESH_PAIR_TABLES         (= esd_mesh_create) the directions n_ij of every line pair,
+ *                                Eq. (avg_volume_metric), and of every facet-correction pair,
+ *                                Eq. (facet_correction), precomputed per element (O(p^(d+1))
+ *                                doubles per element; 42 KB per tetrahedron at p = 4);
+ *   ESD_MESH_METRICS_ON_THE_FLY  only the metric terms G at the volume nodes and J^zeta n at
+ *                                the facet nodes are stored (O(p^d) per element, the paper's
+ *                                storage); the kernel forms every direction from them.
+ * esd_rhs, esd_rk_step, esd_diagnostics and esd_rhs_static_scratch accept both kinds of mesh
+ * and give the same results up to rounding; esd_rhs_vjp, esd_rk_step_vjp and the batch calls
+ * need ESD_MESH_PAIR_TABLES (ESD_ERR_UNSUPPORTED otherwise). */
+enum { ESD_MESH_PAIR_TABLES = 0, ESD_MESH_METRICS_ON_THE_FLY = 1 };
+esd_status esd_mesh_create_ex(const esd_mesh_desc* desc, int options, esd_mesh* out);
 esd_status esd_mesh_destroy(esd_mesh mesh);
 esd_status esd_mesh_info(esd_mesh mesh, esd_info* out);
 

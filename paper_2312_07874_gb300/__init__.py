@@ -47,6 +47,8 @@ ESD_SKEW_EULER, ESD_SKEW_ADVECTION = 0, 1
 
 SYMBOLS = {
     "esd_mesh_create": ([ctypes.POINTER(esd_mesh_desc), ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+    "esd_mesh_create_ex": ([ctypes.POINTER(esd_mesh_desc), ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)],
+                           ctypes.c_int),
     "esd_mesh_destroy": ([ctypes.c_void_p], ctypes.c_int),
     "esd_mesh_info": ([ctypes.c_void_p, ctypes.POINTER(esd_info)], ctypes.c_int),
     "esd_mesh_check": ([ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
@@ -131,7 +133,11 @@ def _stream(stream):
 
 
 # ---- C-named entry points (thin marshalling) -----------------------------------------
-def esd_mesh_create(dim, p, map_nodes, nbr_elem, nbr_face, gamma=1.4, flux=ESD_FLUX_LF):
+ESD_MESH_PAIR_TABLES, ESD_MESH_METRICS_ON_THE_FLY = 0, 1
+
+
+def esd_mesh_create(dim, p, map_nodes, nbr_elem, nbr_face, gamma=1.4, flux=ESD_FLUX_LF,
+                    options=ESD_MESH_PAIR_TABLES):
     X = np.ascontiguousarray(map_nodes, dtype=np.float64)
     ne = np.ascontiguousarray(nbr_elem, dtype=np.int32)
     nf = np.ascontiguousarray(nbr_face, dtype=np.int8)
@@ -139,7 +145,10 @@ def esd_mesh_create(dim, p, map_nodes, nbr_elem, nbr_face, gamma=1.4, flux=ESD_F
                       ne.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), nf.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)),
                       gamma, flux)
     h = ctypes.c_void_p()
-    _check(lib().esd_mesh_create(ctypes.byref(d), ctypes.byref(h)))
+    if options == ESD_MESH_PAIR_TABLES:
+        _check(lib().esd_mesh_create(ctypes.byref(d), ctypes.byref(h)))
+    else:
+        _check(lib().esd_mesh_create_ex(ctypes.byref(d), int(options), ctypes.byref(h)))
     return h
 
 
@@ -292,9 +301,10 @@ def esd_batch_rk_step(b, us, dts, stream=None):
 class Mesh:
     """Owns an esd_mesh handle; state tensors are float64 CUDA [n_elem, N_c, N_p*]."""
 
-    def __init__(self, dim, p, map_nodes, nbr_elem, nbr_face, gamma=1.4, flux="LF"):
+    def __init__(self, dim, p, map_nodes, nbr_elem, nbr_face, gamma=1.4, flux="LF", metrics_on_the_fly=False):
         self.handle = esd_mesh_create(dim, p, map_nodes, nbr_elem, nbr_face, gamma,
-                                      ESD_FLUX_LF if flux == "LF" else ESD_FLUX_EC)
+                                      ESD_FLUX_LF if flux == "LF" else ESD_FLUX_EC,
+                                      ESD_MESH_METRICS_ON_THE_FLY if metrics_on_the_fly else ESD_MESH_PAIR_TABLES)
         self.info = esd_mesh_info(self.handle)
         self.dim, self.p = dim, p
         self.n_elem = self.info["n_elem"]

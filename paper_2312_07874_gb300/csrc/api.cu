@@ -160,6 +160,14 @@ esd_status esd_mesh_create(const esd_mesh_desc* d, esd_mesh* out) {
   return mesh_create(d, kTablesEntropyStable, out);
 }
 
+esd_status esd_mesh_create_ex(const esd_mesh_desc* d, int options, esd_mesh* out) {
+  ESD_RANGE("esd_mesh_create_ex");
+  if (options == ESD_MESH_PAIR_TABLES) return mesh_create(d, kTablesEntropyStable, out);
+  if (options == ESD_MESH_METRICS_ON_THE_FLY) return mesh_create(d, kTablesMetrics, out);
+  if (out) *out = nullptr;
+  return fail(ESD_ERR_ARG, "options must be ESD_MESH_PAIR_TABLES or ESD_MESH_METRICS_ON_THE_FLY");
+}
+
 // Mesh creation with the chosen pair tables (entropy-stable pair directions, or the
 // skew-symmetric form's line-pair coefficients for esd_skew_create).
 static esd_status mesh_create(const esd_mesh_desc* d, int tables, esd_mesh* out) {
@@ -198,6 +206,14 @@ static esd_status mesh_create(const esd_mesh_desc* d, int tables, esd_mesh* out)
   std::vector<double> mt(kMathTabSize);
   build_math_table(mt.data());
   size_t o_mt = push(mt);
+  // on-the-fly pair directions: w_v d eta_k/d xi_l per family, D_k / 4, facet weights
+  std::vector<double> aw((size_t)r.dim * r.dim * r.Nq), dk4((size_t)r.dim * r.n * r.n);
+  for (int k = 0; k < r.dim; ++k) {
+    for (int l = 0; l < r.dim; ++l)
+      for (int v = 0; v < r.Nq; ++v) aw[((size_t)k * r.dim + l) * r.Nq + v] = r.wvol[v] * r.deta[v * 9 + k * 3 + l];
+    for (int ab = 0; ab < r.n * r.n; ++ab) dk4[(size_t)k * r.n * r.n + ab] = 0.25 * r.dl[k][ab];
+  }
+  size_t o_aw = push(aw), o_dk4 = push(dk4), o_wfac = push(r.wfac);
   double* dtab = nullptr;
   int* itab = nullptr;
   if ((st = m->upload(&dtab, dt)) != ESD_OK || (st = m->upload(&itab, r.ints)) != ESD_OK) {
@@ -213,6 +229,11 @@ static esd_status mesh_create(const esd_mesh_desc* d, int tables, esd_mesh* out)
   R.wvol = dtab + o_w;
   R.dense_minv = r.dense_minv;
   R.mtab = dtab + o_mt;
+  R.aw = dtab + o_aw;
+  R.dk4 = dtab + o_dk4;
+  R.wfac = dtab + o_wfac;
+  for (int z = 0; z < 4; ++z)
+    for (int l = 0; l < 3; ++l) R.nhat[z][l] = r.nhat[z][l];
   R.off1 = itab + r.i_off1; R.s12a1 = itab + r.i_s12a1; R.moff = itab + r.i_moff; R.mode = itab + r.i_mode;
   R.s12len = itab + r.i_s12len;
   // per-element data
@@ -232,6 +253,16 @@ static esd_status mesh_create(const esd_mesh_desc* d, int tables, esd_mesh* out)
   if ((tables & kTablesSkew) && (st = m->upload(&m->sdir, H.sdir))) {
     delete m;
     return st;
+  }
+  M.gvol = M.jnf = nullptr;
+  if (tables & kTablesMetrics) {
+    double *gv = nullptr, *jn = nullptr;
+    if ((st = m->upload(&gv, H.gvol)) || (st = m->upload(&jn, H.jnf))) {
+      delete m;
+      return st;
+    }
+    M.gvol = gv;
+    M.jnf = jn;
   }
   M.minv = nullptr;
   if (r.dense_minv) {
@@ -465,6 +496,7 @@ esd_status esd_rhs_vjp(esd_mesh m, const double* u, const double* cot, double* g
   ESD_RANGE("esd_rhs_vjp");
   if (!m) return fail(ESD_ERR_ARG, "null mesh");
   if (esd_status ds = check_device(m->device)) return ds;
+  if (m->M.gvol) return fail(ESD_ERR_UNSUPPORTED, "the VJP needs the stored pair tables (esd_mesh_create)");
   esd_status st;
   if ((st = check_dev(u, "u")) || (st = check_dev(cot, "cot")) || (st = check_dev(grad, "grad"))) return st;
   if (grad == u || grad == cot) return fail(ESD_ERR_ARG, "grad must not alias u or cot");
@@ -481,6 +513,7 @@ esd_status esd_rk_step_vjp(esd_mesh m, const double* ck, double dt, const double
   ESD_RANGE("esd_rk_step_vjp");
   if (!m) return fail(ESD_ERR_ARG, "null mesh");
   if (esd_status ds = check_device(m->device)) return ds;
+  if (m->M.gvol) return fail(ESD_ERR_UNSUPPORTED, "the VJP needs the stored pair tables (esd_mesh_create)");
   esd_status st;
   if ((st = check_dev(ck, "stage_ckpt")) || (st = check_dev(co, "cot_out")) || (st = check_dev(ci, "cot_in")))
     return st;
@@ -553,6 +586,8 @@ esd_status esd_batch_create(const esd_mesh* meshes, int n, esd_batch* out) {
     if (!meshes[i]) return fail(ESD_ERR_ARG, "null mesh in batch");
   for (int i = 0; i < n; ++i)
     if (esd_status ds = check_device(meshes[i]->device)) return ds;
+  for (int i = 0; i < n; ++i)
+    if (meshes[i]->M.gvol) return fail(ESD_ERR_UNSUPPORTED, "batches need meshes with stored pair tables");
   esd_batch b = new esd_batch_s();
   b->meshes.assign(meshes, meshes + n);
   const int sms = sm_count();
@@ -955,8 +990,8 @@ esd_status esd_autotune_kernels(esd_mesh m, const double* u, int kernels, void* 
       if (e == 1) break;
     }
   }
-  // residual adjoint (esd_rhs_vjp): elements per CTA
-  if (kernels & ESD_TUNE_ADJOINT) {
+  // residual adjoint (esd_rhs_vjp): elements per CTA (meshes with stored pair tables)
+  if ((kernels & ESD_TUNE_ADJOINT) && !m->M.gvol) {
     float tbest = 1e30f;
     const int emax = std::max(1, (int)(budget / smem_residual_adj(r, 1)));
     for (int e = 1; e <= emax; ++e) {

@@ -654,18 +654,56 @@ __device__ __forceinline__ void interface_flux(const DevMesh& M, int Nq, int Nfn
   for (int c = 0; c < D + 2; ++c) F[c] *= bj;
 }
 
+// Pair directions formed on the fly from per-node metric terms (meshes created with
+// ESD_MESH_METRICS_ON_THE_FLY), the same quantities the stored tables hold:
+//   volume pair (i at a, j at b) of an eta_k-line:
+//     n_ij / 2 = 1/4 sum_l (Q^(l)_ij - Q^(l)_ji) (G_l.(x_i) + G_l.(x_j)),
+//     Q^(l)_ij = w_i (d eta_k / d xi_l)(xi_i) ell'_{k,b}(eta_{k,a})       (Eq. (avg_volume_metric))
+//   facet pair (volume node i, facet node f of face z):
+//     {{J n}}_if [R^T B]_if / 2 = [R^T B]_if / 4 (G(x_i)^T nhat_z + J^z n(x_f))   (Eq. (facet_correction))
+// G: the element's metric terms [dim*dim][Nq] (component l*dim + m).
+template <int D>
+__device__ __forceinline__ void otf_vol_dir(const DevRef& R, const double* __restrict__ G, int Nq, int k, int a,
+                                            int b, int vi, int vj, double* nh) {
+  const int n = R.n;
+  const double dab = R.dk4[(k * n + a) * n + b], dba = R.dk4[(k * n + b) * n + a];
+  const double* __restrict__ aw = R.aw + (size_t)k * D * Nq;
+  double c[D];
+#pragma unroll
+  for (int l = 0; l < D; ++l) c[l] = fma(dab, aw[l * Nq + vi], -dba * aw[l * Nq + vj]);
+#pragma unroll
+  for (int m = 0; m < D; ++m) {
+    double s = 0.0;
+#pragma unroll
+    for (int l = 0; l < D; ++l) s = fma(c[l], G[(l * D + m) * Nq + vi] + G[(l * D + m) * Nq + vj], s);
+    nh[m] = s;
+  }
+}
+
+// rbq = [R^T B]_if / 4; nz = the face's reference normal; jn = J^z n at the facet node
+template <int D>
+__device__ __forceinline__ void otf_fac_dir(const double* __restrict__ G, int Nq, const double* nz, int vi,
+                                            const double* jn, double rbq, double* nh) {
+#pragma unroll
+  for (int m = 0; m < D; ++m) {
+    double s = jn[m];
+#pragma unroll
+    for (int l = 0; l < D; ++l) s = fma(nz[l], G[(l * D + m) * Nq + vi], s);
+    nh[m] = rbq * s;
+  }
+}
+
 // N facet-correction pairs between facet node f (state Sj) and the line's volume nodes,
-// directions fd[(a * D + k) * T]: acc[a] -= F_a, hs -= F_a.
-template <int D, int N>
+// direction of pair a from dir(a, nh): acc[a] -= F_a, hs -= F_a.
+template <int D, int N, class Dir>
 __device__ __forceinline__ void facet_strip(const double* __restrict__ Sv, int Ntot, int base, int stride,
-                                            const NodeState<D>& Sj, const double* __restrict__ fd, int T,
-                                            const FluxK& K, double (&acc)[N][D + 2], double* hs) {
+                                            const NodeState<D>& Sj, Dir&& dir, const FluxK& K,
+                                            double (&acc)[N][D + 2], double* hs) {
 #pragma unroll
   for (int a = 0; a < N; ++a) {
     const NodeState<D> Si = load_state<D>(Sv, Ntot, base + a * stride);
     double nh[D], F[D + 2];
-#pragma unroll
-    for (int k = 0; k < D; ++k) nh[k] = fd[(a * D + k) * T];
+    dir(a, nh);
     ec_flux_fast<D>(Si, Sj, nh, K, F);
 #pragma unroll
     for (int c = 0; c < D + 2; ++c) {
@@ -689,12 +727,19 @@ __device__ __forceinline__ void facet_strip(const double* __restrict__ Sv, int N
 // tasks sharing a1 update distinct facet nodes in every step -- and finally lifts
 // y = L2J h4 along its eta3-line.  Every thread of the block calls this (phase 2 has
 // barriers); `act` marks the threads that own a task.
-template <int D, int N>
+template <int D, int N, bool OTF = false>
 __device__ __forceinline__ void line_task(int ph, int t, bool act, const DevRef& R, const DevMesh& M, int64_t eg,
                                           const double* __restrict__ Sv, const double* __restrict__ Sf, double* r,
                                           double* h4, const double* __restrict__ vdir,
                                           const double* __restrict__ fdir, const FluxK& K) {
   constexpr int NC = D + 2;
+  // on-the-fly directions: the element's metric terms and facet normals
+  const double* __restrict__ G = OTF ? M.gvol + eg * (int64_t)D * D * R.Nq : nullptr;
+  const double* __restrict__ JN = OTF ? M.jnf + eg * (int64_t)D * R.Nfn : nullptr;
+  auto jn_at = [&](int f, double* jn) {
+#pragma unroll
+    for (int m = 0; m < D; ++m) jn[m] = JN[m * R.Nfn + f];
+  };
   const int Nq = R.Nq, Nfn = R.Nfn, Nqf = R.Nqf, T = R.T, Ntot = R.Ntot;
   int base, stride;
   if (D == 2) {
@@ -720,8 +765,12 @@ __device__ __forceinline__ void line_task(int ph, int t, bool act, const DevRef&
         const NodeState<D> Si = load_state<D>(Sv, Ntot, base + a * stride);
         const NodeState<D> Sj = load_state<D>(Sv, Ntot, base + b * stride);
         double nh[D], F[NC];
+        if constexpr (OTF) {
+          otf_vol_dir<D>(R, G, Nq, ph, a, b, base + a * stride, base + b * stride, nh);
+        } else {
 #pragma unroll
-        for (int k = 0; k < D; ++k) nh[k] = vd[(m * D + k) * T];
+          for (int k = 0; k < D; ++k) nh[k] = vd[(m * D + k) * T];
+        }
         ec_flux_fast<D>(Si, Sj, nh, K, F);
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
@@ -737,9 +786,21 @@ __device__ __forceinline__ void line_task(int ph, int t, bool act, const DevRef&
         double hs[NC];
         interface_flux<D>(M, Nq, Nfn, Ntot, eg, f, Sf, K, hs);
         const NodeState<D> Sj = load_state<D>(Sf, Ntot, f);
-        facet_strip<D, N>(Sv, Ntot, base, stride, Sj, fdir + R.fph_off[0] + (size_t)zz * N * D * T + t, T, K, acc,
-                          hs);
-        const double* l = zz == 0 ? R.l1p : R.l1m;   // lift of facets 2, 3 along the eta1-line
+        const double* l = zz == 0 ? R.l1p : R.l1m;   // R entries along the eta1-line (and the lift)
+        if constexpr (OTF) {
+          double jn[D];
+          jn_at(f, jn);
+          const double wq = 0.25 * R.wfac[f];
+          facet_strip<D, N>(Sv, Ntot, base, stride, Sj, [&](int a, double* nh) {
+            otf_fac_dir<D>(G, Nq, R.nhat[1 + zz], base + a * stride, jn, wq * l[a], nh);
+          }, K, acc, hs);
+        } else {
+          const double* fd = fdir + R.fph_off[0] + (size_t)zz * N * D * T + t;
+          facet_strip<D, N>(Sv, Ntot, base, stride, Sj, [&](int a, double* nh) {
+#pragma unroll
+            for (int k = 0; k < D; ++k) nh[k] = fd[(a * D + k) * T];
+          }, K, acc, hs);
+        }
 #pragma unroll
         for (int a = 0; a < N; ++a) {
           const double la = l[a];
@@ -752,7 +813,20 @@ __device__ __forceinline__ void line_task(int ph, int t, bool act, const DevRef&
       double hs[NC];
       interface_flux<D>(M, Nq, Nfn, Ntot, eg, f, Sf, K, hs);
       const NodeState<D> Sj = load_state<D>(Sf, Ntot, f);
-      facet_strip<D, N>(Sv, Ntot, base, stride, Sj, fdir + R.fph_off[1] + t, T, K, acc, hs);
+      if constexpr (OTF) {
+        double jn[D];
+        jn_at(f, jn);
+        const double wq = 0.25 * R.wfac[f];
+        facet_strip<D, N>(Sv, Ntot, base, stride, Sj, [&](int a, double* nh) {
+          otf_fac_dir<D>(G, Nq, R.nhat[0], base + a * stride, jn, wq * R.l2m[a], nh);
+        }, K, acc, hs);
+      } else {
+        const double* fd = fdir + R.fph_off[1] + t;
+        facet_strip<D, N>(Sv, Ntot, base, stride, Sj, [&](int a, double* nh) {
+#pragma unroll
+          for (int k = 0; k < D; ++k) nh[k] = fd[(a * D + k) * T];
+        }, K, acc, hs);
+      }
 #pragma unroll
       for (int a = 0; a < N; ++a) {   // lift of facet 1 along the eta2-line
         const double la = R.l2m[a];
@@ -768,7 +842,7 @@ __device__ __forceinline__ void line_task(int ph, int t, bool act, const DevRef&
   }
   if (D == 3 && ph == 2) {
     const int a1 = t % N, a2 = t / N;
-    const double* fd4 = act ? fdir + R.fph_off[3] + t : nullptr;
+    const double* fd4 = (act && !OTF) ? fdir + R.fph_off[3] + t : nullptr;
 #pragma unroll 1
     for (int k = 0; k < N; ++k) {
       if (act) {
@@ -778,7 +852,20 @@ __device__ __forceinline__ void line_task(int ph, int t, bool act, const DevRef&
         double hs[NC];
 #pragma unroll
         for (int c = 0; c < NC; ++c) hs[c] = 0.0;
-        facet_strip<D, N>(Sv, Ntot, base, stride, Sj, fd4 + (size_t)bp * N * D * T, T, K, acc, hs);
+        if constexpr (OTF) {
+          double jn[D];
+          jn_at(3 * Nqf + j, jn);
+          const double wq = 0.25 * R.wfac[3 * Nqf + j] * R.L2J[bp * N + a2];
+          facet_strip<D, N>(Sv, Ntot, base, stride, Sj, [&](int a, double* nh) {
+            otf_fac_dir<D>(G, Nq, R.nhat[3], base + a * stride, jn, wq * R.l3m[a], nh);
+          }, K, acc, hs);
+        } else {
+          const double* fd = fd4 + (size_t)bp * N * D * T;
+          facet_strip<D, N>(Sv, Ntot, base, stride, Sj, [&](int a, double* nh) {
+#pragma unroll
+            for (int kk = 0; kk < D; ++kk) nh[kk] = fd[(a * D + kk) * T];
+          }, K, acc, hs);
+        }
 #pragma unroll
         for (int c = 0; c < NC; ++c) h4[c * Nqf + j] += hs[c];
       }
@@ -810,7 +897,7 @@ __device__ __forceinline__ void line_task(int ph, int t, bool act, const DevRef&
   }
 }
 
-template <int D, int N>
+template <int D, int N, bool OTF = false>
 __device__ void residual_tile(const DevRef& R, const DevMesh& M, int64_t e0, int E, const Epilogue& ep) {
   extern __shared__ double sm_raw[];
   unsigned long long* bar = reinterpret_cast<unsigned long long*>(sm_raw);
@@ -866,13 +953,13 @@ __device__ void residual_tile(const DevRef& R, const DevMesh& M, int64_t e0, int
     const bool act = el < E;
     const int elc = act ? el : 0;
     const int64_t eg = e0 + elc;
-    const double* vdir = act ? M.vdir + eg * (int64_t)R.nvp * D : nullptr;
-    const double* fdir = act ? M.fdir + eg * (int64_t)R.nfp * D : nullptr;
+    const double* vdir = (act && !OTF) ? M.vdir + eg * (int64_t)R.nvp * D : nullptr;
+    const double* fdir = (act && !OTF) ? M.fdir + eg * (int64_t)R.nfp * D : nullptr;
     double* base = sm + elc * pe;
 #pragma unroll 1
     for (int ph = 0; ph < D; ++ph) {
-      line_task<D, N>(ph, t, act, R, M, eg, base + Ly.oS, base + Ly.oS + Nq, base + Ly.oR, base + Ly.oH4, vdir,
-                      fdir, K);
+      line_task<D, N, OTF>(ph, t, act, R, M, eg, base + Ly.oS, base + Ly.oS + Nq, base + Ly.oR, base + Ly.oH4, vdir,
+                           fdir, K);
       __syncthreads();
     }
   }

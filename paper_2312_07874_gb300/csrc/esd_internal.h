@@ -61,11 +61,14 @@ struct HostMesh {
   std::vector<double> xvol;           // [E][Nq][dim]
   std::vector<double> minv;           // [E][Np][Np] V^T (W/J) V (when ref.dense_minv)
   std::vector<double> sdir;           // [E][dim][n(n-1)][dim][T] skew-form line-pair coefficients
+  std::vector<double> gvol;           // [E][dim*dim][Nq] metric terms G_lm (component l*dim+m)
+  std::vector<double> jnf;            // [E][dim][Nfn] G^T nhat at the facet nodes (J^zeta n)
 };
 
 // which mesh-static pair tables build_host_mesh computes
 constexpr int kTablesEntropyStable = 1;   // vdir, fdir (the entropy-stable residual)
 constexpr int kTablesSkew = 2;            // sdir (the skew-symmetric form, skew.cuh)
+constexpr int kTablesMetrics = 4;         // gvol, jnf (pair directions formed on the fly)
 
 esd_status build_ref(int dim, int p, RefTables* out, std::string* err);
 esd_status build_host_mesh(const esd_mesh_desc& d, HostMesh* out, std::string* err,
@@ -89,6 +92,11 @@ struct DevRef {
   const double* wvol;
   int dense_minv;
   const double* mtab;   // kMathTabSize doubles
+  // pair directions formed on the fly (meshes created with ESD_MESH_METRICS_ON_THE_FLY)
+  const double* aw;     // [dim (family k)][dim (l)][Nq]: w_v (d eta_k / d xi_l)(xi_v)
+  const double* dk4;    // [dim][n*n]: dl[k][a*n+b] / 4
+  const double* wfac;   // [Nfn] facet quadrature weights
+  double nhat[4][3];    // reference facet normals
 };
 
 // bits of DevMesh::flag (read and cleared by esd_mesh_check)
@@ -105,6 +113,8 @@ struct DevMesh {
   int* flag;        // admissibility flag
   double gamma;
   int lf;
+  const double* gvol;   // [E][dim*dim][Nq] metric terms, when directions are formed on the fly
+  const double* jnf;    // [E][dim][Nfn] J^zeta n at the facet nodes (same)
 };
 
 struct LaunchCfg {
@@ -176,6 +186,13 @@ cudaError_t launch_residual_d3_hi(const DevRef& R, const DevMesh& M, const Launc
 cudaError_t launch_residual_batch_d3_hi(int n, const BatchMesh* meshes, const BatchItem* items, int nitems,
                                         int grid, int threads, size_t smem, cudaStream_t s);
 cudaError_t set_residual_smem_d3_hi(int lim);
+// pair directions formed on the fly (residual_otf_d2.cu, residual_otf_d3.cu)
+cudaError_t launch_residual_otf_d2(const DevRef& R, const DevMesh& M, const LaunchCfg& L, const Epilogue& ep,
+                                   cudaStream_t s);
+cudaError_t launch_residual_otf_d3(const DevRef& R, const DevMesh& M, const LaunchCfg& L, const Epilogue& ep,
+                                   cudaStream_t s);
+cudaError_t set_residual_otf_smem_d2(int lim);
+cudaError_t set_residual_otf_smem_d3(int lim);
 cudaError_t launch_reduce_diag(const double* part, int64_t E, int ncol, double* out, cudaStream_t s);
 cudaError_t launch_integrals(const DevRef& R, const DevMesh& M, const LaunchCfg& L, const double* u, double* part,
                              cudaStream_t s);

@@ -669,6 +669,7 @@ cudaError_t set_smem_limits(const LaunchCfg& L, int dim) {
     e = cudaFuncSetAttribute(integrals_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     if (e) return e;
     e = set_residual_smem_d2(lim);
+    if (!e) e = set_residual_otf_smem_d2(lim);
   } else {
     e = cudaFuncSetAttribute(project_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     if (e) return e;
@@ -683,6 +684,7 @@ cudaError_t set_smem_limits(const LaunchCfg& L, int dim) {
     e = cudaFuncSetAttribute(integrals_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     if (e) return e;
     e = set_residual_smem_d3(lim);
+    if (!e) e = set_residual_otf_smem_d3(lim);
   }
   return e;
 }
@@ -699,6 +701,8 @@ cudaError_t launch_project(const DevRef& R, const DevMesh& M, const LaunchCfg& L
 
 cudaError_t launch_residual(const DevRef& R, const DevMesh& M, const LaunchCfg& L, const Epilogue& ep,
                             cudaStream_t s) {
+  if (M.gvol)   // pair directions formed on the fly (ESD_MESH_METRICS_ON_THE_FLY)
+    return R.dim == 2 ? launch_residual_otf_d2(R, M, L, ep, s) : launch_residual_otf_d3(R, M, L, ep, s);
   return R.dim == 2 ? launch_residual_d2(R, M, L, ep, s) : launch_residual_d3(R, M, L, ep, s);
 }
 

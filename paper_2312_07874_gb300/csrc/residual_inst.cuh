@@ -7,11 +7,11 @@
 
 namespace esd {
 
-template <int D, int N>
+template <int D, int N, bool OTF = false>
 __global__ void residual_kernel(DevRef R, DevMesh M, int epc, Epilogue ep) {
   const int64_t e0 = (int64_t)blockIdx.x * epc;
   const int E = (int)((M.E - e0) < (int64_t)epc ? (M.E - e0) : (int64_t)epc);
-  residual_tile<D, N>(R, M, e0, E, ep);
+  residual_tile<D, N, OTF>(R, M, e0, E, ep);
 }
 
 // Batched execution of many meshes with the same (dimension, degree): a persistent grid
@@ -48,6 +48,24 @@ cudaError_t set_residual_smem_n(int lim) {
   cudaError_t e = cudaFuncSetAttribute(residual_kernel<D, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   if (e) return e;
   return cudaFuncSetAttribute(residual_batch_kernel<D, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+}
+
+}  // namespace esd
+
+namespace esd {
+
+// The residual kernel with pair directions formed on the fly (residual_otf_*.cu).
+template <int D, int N>
+cudaError_t launch_residual_otf_n(const DevRef& R, const DevMesh& M, const LaunchCfg& L, const Epilogue& ep,
+                                  cudaStream_t s) {
+  const unsigned grid = (unsigned)((M.E + L.eb - 1) / L.eb);
+  residual_kernel<D, N, true><<<grid, L.tb, L.sb, s>>>(R, M, L.eb, ep);
+  return cudaGetLastError();
+}
+
+template <int D, int N>
+cudaError_t set_residual_otf_smem_n(int lim) {
+  return cudaFuncSetAttribute(residual_kernel<D, N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
 }
 
 }  // namespace esd

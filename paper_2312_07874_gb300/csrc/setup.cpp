@@ -467,6 +467,7 @@ double det(int d, const double* A) {  // A[m*d+k] = d x_m / d xi_k
 
 esd_status build_host_mesh(const esd_mesh_desc& d, HostMesh* H, std::string* err, int tables) {
   const bool es = (tables & kTablesEntropyStable) != 0, skew = (tables & kTablesSkew) != 0;
+  const bool metrics = (tables & kTablesMetrics) != 0;
   esd_status st = build_ref(d.dim, d.p, &H->ref, err);
   if (st != ESD_OK) return st;
   const RefTables& r = H->ref;
@@ -492,6 +493,8 @@ esd_status build_host_mesh(const esd_mesh_desc& d, HostMesh* H, std::string* err
   H->vdir.assign(es ? (size_t)E * r.nvp * dim : 0, 0.0);
   H->fdir.assign(es ? (size_t)E * r.nfp * dim : 0, 0.0);
   H->sdir.assign(skew ? (size_t)E * dim * T * n * (n - 1) * dim : 0, 0.0);
+  H->gvol.assign(metrics ? (size_t)E * dim * dim * Nq : 0, 0.0);
+  H->jnf.assign(metrics ? (size_t)E * dim * Nfn : 0, 0.0);
   H->wj.assign((size_t)E * Nq, 0.0);
   H->wdj.assign((size_t)E * Nq, 0.0);
   H->bj.assign((size_t)E * Nfn, 0.0);
@@ -623,10 +626,16 @@ esd_status build_host_mesh(const esd_mesh_desc& d, HostMesh* H, std::string* err
         nn = std::sqrt(nn);
         for (int m = 0; m < dim; ++m) {
           Jnfac[((size_t)e * Nfn + f) * dim + m] = Jn[m];
+          if (metrics) H->jnf[((size_t)e * dim + m) * Nfn + f] = Jn[m];
           H->nrm[((size_t)e * dim + m) * Nfn + f] = Jn[m] / nn;
         }
         H->bj[(size_t)e * Nfn + f] = r.wfac[f] * nn;
       }
+      if (metrics)   // metric terms at the volume nodes, component-major
+        for (int v = 0; v < Nq; ++v)
+          for (int l = 0; l < dim; ++l)
+            for (int mm = 0; mm < dim; ++mm)
+              H->gvol[((size_t)e * dim * dim + l * dim + mm) * Nq + v] = G[v * 9 + l * 3 + mm];
       // line node indices: node a of line t of phase ph
       auto line_node = [&](int ph, int t, int a) {
         if (dim == 2) return ph == 0 ? a + n * t : t + n * a;

@@ -228,3 +228,44 @@ def test_affine_triangles_rhs_and_ten_rk4_steps():
         ref = rk4_step(lambda v: D.rhs(v, "sparse"), ref, dt)
     err = rel_err_per_var(u.cpu().numpy() - um, ref - um)
     assert np.all(err < TOL), err
+
+
+OTF_CASES = [(2, 4, 3, "vortex"), (2, 3, 8, "vortex"), (3, 3, 2, "tgv"), (3, 3, 4, "density_wave"),
+             (3, 3, 4, "tgv"), (3, 3, 7, "density_wave")]
+
+
+@pytest.mark.parametrize("dim,M,p,state", OTF_CASES)
+def test_metrics_on_the_fly_parity(dim, M, p, state):
+    """A mesh created with ESD_MESH_METRICS_ON_THE_FLY forms every pair direction from the
+    per-node metric terms in the kernel: the same checks against the oracle as the stored
+    tables, the same result as the stored-table mesh up to rounding, and an RK4 step; the
+    VJP and batches report ESD_ERR_UNSUPPORTED."""
+    import torch
+    import paper_2312_07874_gb300 as E
+    mesh, X, D, um = workload(dim, M, p, True, "LF", state)
+    g_otf = E.Mesh(dim, p, X, mesh.nbr_elem, mesh.nbr_face, flux="LF", metrics_on_the_fly=True)
+    g_tab = gpu_mesh(dim, p, X, mesh)
+    u = to_dev(um)
+    a = g_otf.rhs(u).cpu().numpy()
+    b = g_tab.rhs(u).cpu().numpy()
+    g_otf.check()
+    if p <= 4:
+        check_parity(f"on-the-fly directions dim={dim} M={M} p={p} {state}", a, D, X, um, n_exact=2, seed=p)
+    else:
+        rng = np.random.default_rng(p)
+        sample = np.sort(rng.choice(D.E, size=3, replace=False))
+        check_parity(f"on-the-fly directions dim={dim} M={M} p={p} {state} (sample)", a[sample], D, X, um,
+                     elems=sample, n_exact=1, seed=p)
+    # against the stored-table mesh: relative to the term scale the two differ by rounding only
+    assert np.all(rel_err_per_var(a, b) < 1e-9)
+    assert g_otf.info["device_bytes"] < g_tab.info["device_bytes"]
+    ua, ub = u.clone(), u.clone()
+    g_otf.rk_step(ua, 1e-3)
+    g_tab.rk_step(ub, 1e-3)
+    torch.cuda.synchronize()
+    assert np.all(rel_err_per_var(ua.cpu().numpy() - um, ub.cpu().numpy() - um) < 1e-9)
+    g = torch.empty_like(u)
+    assert E.lib().esd_rhs_vjp(g_otf.handle, E._ptr(u), E._ptr(u), E._ptr(g), None) == -7
+    with pytest.raises(E.EsdError) as ex:
+        E.esd_batch_create([g_otf.handle])
+    assert ex.value.status == -7
