@@ -277,11 +277,16 @@ static esd_status mesh_create(const esd_mesh_desc* d, int tables, esd_mesh* out)
   const size_t nmodal = (size_t)m->E * m->nc * r.Np;
   if ((st = m->alloc(&M.states, nstate)) || (st = m->alloc(&M.cfac, (size_t)m->E * r.Nfn)) ||
       (st = m->alloc(&M.flag, 1)) || (st = m->alloc(&m->ws_acc, nmodal)) || (st = m->alloc(&m->ws_stage, nmodal)) ||
-      (st = m->alloc(&m->ws_diag, (size_t)m->E * (m->nc + 2))) ||
-      (st = m->alloc(&m->ws_qbar, (size_t)m->E * m->nc * r.Ntot)) ||
-      (st = m->alloc(&m->ws_qext, (size_t)m->E * m->nc * r.Nfn)) || (st = m->alloc(&m->ws_adj[0], nmodal)) ||
-      (st = m->alloc(&m->ws_adj[1], nmodal)) || (st = m->alloc(&m->ws_adj[2], nmodal)) ||
-      (st = m->alloc(&m->ws_adj[3], nmodal))) {
+      (st = m->alloc(&m->ws_diag, (size_t)m->E * (m->nc + 2)))) {
+    delete m;
+    return st;
+  }
+  // the VJP's workspaces, only where the VJP can run (meshes with the stored pair tables)
+  if ((tables & kTablesEntropyStable) &&
+      ((st = m->alloc(&m->ws_qbar, (size_t)m->E * m->nc * r.Ntot)) ||
+       (st = m->alloc(&m->ws_qext, (size_t)m->E * m->nc * r.Nfn)) || (st = m->alloc(&m->ws_adj[0], nmodal)) ||
+       (st = m->alloc(&m->ws_adj[1], nmodal)) || (st = m->alloc(&m->ws_adj[2], nmodal)) ||
+       (st = m->alloc(&m->ws_adj[3], nmodal)))) {
     delete m;
     return st;
   }
@@ -947,7 +952,7 @@ esd_status esd_autotune_kernels(esd_mesh m, const double* u, int kernels, void* 
     if (e0) return cuda_fail(e0, "autotune projection");
     Epilogue ep{};
     ep.mode = 0;
-    ep.dudt = m->ws_adj[0];
+    ep.dudt = m->ws_stage;   // scratch output (the RK stage buffer; autotuning drops captured graphs)
     float tbest = 1e30f;
     const int emax = std::min(std::max(1, (int)(budget / smem_residual(r, 1))), std::max(1, 1024 / r.T));
     for (int e = 1; e <= emax; ++e) {
@@ -966,8 +971,8 @@ esd_status esd_autotune_kernels(esd_mesh m, const double* u, int kernels, void* 
     }
   }
   // projection adjoint (esd_rhs_vjp): elements per CTA x threads, with the residual
-  // adjoint's current shape
-  if (kernels & ESD_TUNE_ADJOINT) {
+  // adjoint's current shape (meshes with stored pair tables)
+  if ((kernels & ESD_TUNE_ADJOINT) && !m->M.gvol) {
     float tbest = 1e30f;
     const int emax = std::max(1, (int)(budget / smem_project(r, 1)));
     for (int e = emax; e >= 1; e = e > 1 ? e / 2 : 0) {
