@@ -694,22 +694,29 @@ __device__ __forceinline__ void otf_fac_dir(const double* __restrict__ G, int Nq
 }
 
 // N facet-correction pairs between facet node f (state Sj) and the line's volume nodes,
-// direction of pair a from dir(a, nh): acc[a] -= F_a, hs -= F_a.
-template <int D, int N, class Dir>
+// direction of pair a from dir(a, nh): node a's residual -= F_a (through sub(a, F)),
+// hs -= F_a.
+// UNROLL: unrolled over the line (register accumulators need constant indices); otherwise a
+// loop (accumulation in shared memory).
+template <int D, int N, bool UNROLL, class Dir, class Sub>
 __device__ __forceinline__ void facet_strip(const double* __restrict__ Sv, int Ntot, int base, int stride,
-                                            const NodeState<D>& Sj, Dir&& dir, const FluxK& K,
-                                            double (&acc)[N][D + 2], double* hs) {
-#pragma unroll
-  for (int a = 0; a < N; ++a) {
+                                            const NodeState<D>& Sj, Dir&& dir, const FluxK& K, Sub&& sub,
+                                            double* hs) {
+  auto pair = [&](int a) {
     const NodeState<D> Si = load_state<D>(Sv, Ntot, base + a * stride);
     double nh[D], F[D + 2];
     dir(a, nh);
     ec_flux_fast<D>(Si, Sj, nh, K, F);
+    sub(a, F);
 #pragma unroll
-    for (int c = 0; c < D + 2; ++c) {
-      acc[a][c] -= F[c];
-      hs[c] -= F[c];
-    }
+    for (int c = 0; c < D + 2; ++c) hs[c] -= F[c];
+  };
+  if constexpr (UNROLL) {
+#pragma unroll
+    for (int a = 0; a < N; ++a) pair(a);
+  } else {
+#pragma unroll 1
+    for (int a = 0; a < N; ++a) pair(a);
   }
 }
 
@@ -750,32 +757,86 @@ __device__ __forceinline__ void line_task(int ph, int t, bool act, const DevRef&
     else if (ph == 1) { base = (t % N) + N * N * (t / N); stride = N; }
     else { base = t; stride = N * N; }
   }
+  // Node residuals of the line: in registers (acc, unrolled pair loops), or -- where N
+  // accumulators no longer fit in registers beside the flux (tetrahedra N >= 6, triangles
+  // N >= 8) -- directly in the shared residual r, which this task owns for its line in
+  // this phase, with node a's running sum over its pairs in registers.
+  constexpr bool SACC = D == 3 ? N >= 6 : N >= 8;
   double acc[N][NC];
+  if constexpr (!SACC) {
 #pragma unroll
-  for (int a = 0; a < N; ++a)
+    for (int a = 0; a < N; ++a)
 #pragma unroll
-    for (int c = 0; c < NC; ++c) acc[a][c] = 0.0;
+      for (int c = 0; c < NC; ++c) acc[a][c] = 0.0;
+  }
+  auto node_fma = [&](int a, int c, double x, double y) {   // residual(a, c) += x * y
+    if constexpr (SACC) {
+      double& ra = r[c * Nq + base + a * stride];
+      ra = fma(x, y, ra);
+    } else {
+      acc[a][c] = fma(x, y, acc[a][c]);
+    }
+  };
+  auto sub_flux = [&](int a, const double* F) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      if constexpr (SACC)
+        r[c * Nq + base + a * stride] -= F[c];
+      else
+        acc[a][c] -= F[c];
+    }
+  };
   if (act) {
     constexpr int Lv = N * (N - 1) / 2;
     const double* vd = vdir + (size_t)ph * Lv * D * T + t;
-#pragma unroll
-    for (int a = 0, m = 0; a < N; ++a) {
-#pragma unroll
-      for (int b = a + 1; b < N; ++b, ++m) {
+    if constexpr (SACC) {
+      int m = 0;
+#pragma unroll 1
+      for (int a = 0; a < N; ++a) {
         const NodeState<D> Si = load_state<D>(Sv, Ntot, base + a * stride);
-        const NodeState<D> Sj = load_state<D>(Sv, Ntot, base + b * stride);
-        double nh[D], F[NC];
-        if constexpr (OTF) {
-          otf_vol_dir<D>(R, G, Nq, ph, a, b, base + a * stride, base + b * stride, nh);
-        } else {
+        double ra[NC];
 #pragma unroll
-          for (int k = 0; k < D; ++k) nh[k] = vd[(m * D + k) * T];
+        for (int c = 0; c < NC; ++c) ra[c] = 0.0;
+#pragma unroll 1
+        for (int b = a + 1; b < N; ++b, ++m) {
+          const NodeState<D> Sj = load_state<D>(Sv, Ntot, base + b * stride);
+          double nh[D], F[NC];
+          if constexpr (OTF) {
+            otf_vol_dir<D>(R, G, Nq, ph, a, b, base + a * stride, base + b * stride, nh);
+          } else {
+#pragma unroll
+            for (int k = 0; k < D; ++k) nh[k] = vd[(m * D + k) * T];
+          }
+          ec_flux_fast<D>(Si, Sj, nh, K, F);
+#pragma unroll
+          for (int c = 0; c < NC; ++c) {
+            ra[c] -= F[c];
+            r[c * Nq + base + b * stride] += F[c];
+          }
         }
-        ec_flux_fast<D>(Si, Sj, nh, K, F);
 #pragma unroll
-        for (int c = 0; c < NC; ++c) {
-          acc[a][c] -= F[c];
-          acc[b][c] += F[c];
+        for (int c = 0; c < NC; ++c) r[c * Nq + base + a * stride] += ra[c];
+      }
+    } else {
+#pragma unroll
+      for (int a = 0, m = 0; a < N; ++a) {
+#pragma unroll
+        for (int b = a + 1; b < N; ++b, ++m) {
+          const NodeState<D> Si = load_state<D>(Sv, Ntot, base + a * stride);
+          const NodeState<D> Sj = load_state<D>(Sv, Ntot, base + b * stride);
+          double nh[D], F[NC];
+          if constexpr (OTF) {
+            otf_vol_dir<D>(R, G, Nq, ph, a, b, base + a * stride, base + b * stride, nh);
+          } else {
+#pragma unroll
+            for (int k = 0; k < D; ++k) nh[k] = vd[(m * D + k) * T];
+          }
+          ec_flux_fast<D>(Si, Sj, nh, K, F);
+#pragma unroll
+          for (int c = 0; c < NC; ++c) {
+            acc[a][c] -= F[c];
+            acc[b][c] += F[c];
+          }
         }
       }
     }
@@ -791,21 +852,21 @@ __device__ __forceinline__ void line_task(int ph, int t, bool act, const DevRef&
           double jn[D];
           jn_at(f, jn);
           const double wq = 0.25 * R.wfac[f];
-          facet_strip<D, N>(Sv, Ntot, base, stride, Sj, [&](int a, double* nh) {
+          facet_strip<D, N, !SACC>(Sv, Ntot, base, stride, Sj, [&](int a, double* nh) {
             otf_fac_dir<D>(G, Nq, R.nhat[1 + zz], base + a * stride, jn, wq * l[a], nh);
-          }, K, acc, hs);
+          }, K, sub_flux, hs);
         } else {
           const double* fd = fdir + R.fph_off[0] + (size_t)zz * N * D * T + t;
-          facet_strip<D, N>(Sv, Ntot, base, stride, Sj, [&](int a, double* nh) {
+          facet_strip<D, N, !SACC>(Sv, Ntot, base, stride, Sj, [&](int a, double* nh) {
 #pragma unroll
             for (int k = 0; k < D; ++k) nh[k] = fd[(a * D + k) * T];
-          }, K, acc, hs);
+          }, K, sub_flux, hs);
         }
 #pragma unroll
         for (int a = 0; a < N; ++a) {
           const double la = l[a];
 #pragma unroll
-          for (int c = 0; c < NC; ++c) acc[a][c] = fma(-la, hs[c], acc[a][c]);
+          for (int c = 0; c < NC; ++c) node_fma(a, c, -la, hs[c]);
         }
       }
     } else if (ph == 1) {
@@ -817,21 +878,21 @@ __device__ __forceinline__ void line_task(int ph, int t, bool act, const DevRef&
         double jn[D];
         jn_at(f, jn);
         const double wq = 0.25 * R.wfac[f];
-        facet_strip<D, N>(Sv, Ntot, base, stride, Sj, [&](int a, double* nh) {
+        facet_strip<D, N, !SACC>(Sv, Ntot, base, stride, Sj, [&](int a, double* nh) {
           otf_fac_dir<D>(G, Nq, R.nhat[0], base + a * stride, jn, wq * R.l2m[a], nh);
-        }, K, acc, hs);
+        }, K, sub_flux, hs);
       } else {
         const double* fd = fdir + R.fph_off[1] + t;
-        facet_strip<D, N>(Sv, Ntot, base, stride, Sj, [&](int a, double* nh) {
+        facet_strip<D, N, !SACC>(Sv, Ntot, base, stride, Sj, [&](int a, double* nh) {
 #pragma unroll
           for (int k = 0; k < D; ++k) nh[k] = fd[(a * D + k) * T];
-        }, K, acc, hs);
+        }, K, sub_flux, hs);
       }
 #pragma unroll
       for (int a = 0; a < N; ++a) {   // lift of facet 1 along the eta2-line
         const double la = R.l2m[a];
 #pragma unroll
-        for (int c = 0; c < NC; ++c) acc[a][c] = fma(-la, hs[c], acc[a][c]);
+        for (int c = 0; c < NC; ++c) node_fma(a, c, -la, hs[c]);
       }
     } else if (D == 3) {
       double hs[NC];
@@ -856,15 +917,15 @@ __device__ __forceinline__ void line_task(int ph, int t, bool act, const DevRef&
           double jn[D];
           jn_at(3 * Nqf + j, jn);
           const double wq = 0.25 * R.wfac[3 * Nqf + j] * R.L2J[bp * N + a2];
-          facet_strip<D, N>(Sv, Ntot, base, stride, Sj, [&](int a, double* nh) {
+          facet_strip<D, N, !SACC>(Sv, Ntot, base, stride, Sj, [&](int a, double* nh) {
             otf_fac_dir<D>(G, Nq, R.nhat[3], base + a * stride, jn, wq * R.l3m[a], nh);
-          }, K, acc, hs);
+          }, K, sub_flux, hs);
         } else {
           const double* fd = fd4 + (size_t)bp * N * D * T;
-          facet_strip<D, N>(Sv, Ntot, base, stride, Sj, [&](int a, double* nh) {
+          facet_strip<D, N, !SACC>(Sv, Ntot, base, stride, Sj, [&](int a, double* nh) {
 #pragma unroll
             for (int kk = 0; kk < D; ++kk) nh[kk] = fd[(a * D + kk) * T];
-          }, K, acc, hs);
+          }, K, sub_flux, hs);
         }
 #pragma unroll
         for (int c = 0; c < NC; ++c) h4[c * Nqf + j] += hs[c];
@@ -885,15 +946,17 @@ __device__ __forceinline__ void line_task(int ph, int t, bool act, const DevRef&
       for (int a = 0; a < N; ++a) {
         const double la = R.l3m[a];
 #pragma unroll
-        for (int c = 0; c < NC; ++c) acc[a][c] = fma(-la, y[c], acc[a][c]);
+        for (int c = 0; c < NC; ++c) node_fma(a, c, -la, y[c]);
       }
     }
   }
-  if (act) {
+  if constexpr (!SACC) {
+    if (act) {
 #pragma unroll
-    for (int a = 0; a < N; ++a)
+      for (int a = 0; a < N; ++a)
 #pragma unroll
-      for (int c = 0; c < NC; ++c) r[c * Nq + base + a * stride] += acc[a][c];
+        for (int c = 0; c < NC; ++c) r[c * Nq + base + a * stride] += acc[a][c];
+    }
   }
 }
 
