@@ -694,48 +694,51 @@ __device__ __forceinline__ void otf_fac_dir(const double* __restrict__ G, int Nq
 }
 
 // N facet-correction pairs between facet node f (state Sj) and the line's volume nodes,
-// direction of pair a from dir(a, nh): node a's residual -= F_a (through sub(a, F)),
-// hs -= F_a.
-// UNROLL: unrolled over the line (register accumulators need constant indices); otherwise a
-// loop (accumulation in shared memory).
-template <int D, int N, bool UNROLL, class Dir, class Sub>
+// direction of pair a from dir(a, nh): acc[a] -= F_a, hs -= F_a (register accumulators,
+// unrolled over the line).
+template <int D, int N, class Dir>
 __device__ __forceinline__ void facet_strip(const double* __restrict__ Sv, int Ntot, int base, int stride,
-                                            const NodeState<D>& Sj, Dir&& dir, const FluxK& K, Sub&& sub,
-                                            double* hs) {
-  auto pair = [&](int a) {
+                                            const NodeState<D>& Sj, Dir&& dir, const FluxK& K,
+                                            double (&acc)[N][D + 2], double* hs) {
+#pragma unroll
+  for (int a = 0; a < N; ++a) {
     const NodeState<D> Si = load_state<D>(Sv, Ntot, base + a * stride);
     double nh[D], F[D + 2];
     dir(a, nh);
     ec_flux_fast<D>(Si, Sj, nh, K, F);
-    sub(a, F);
 #pragma unroll
-    for (int c = 0; c < D + 2; ++c) hs[c] -= F[c];
-  };
-  if constexpr (UNROLL) {
-#pragma unroll
-    for (int a = 0; a < N; ++a) pair(a);
-  } else {
-#pragma unroll 1
-    for (int a = 0; a < N; ++a) pair(a);
+    for (int c = 0; c < D + 2; ++c) {
+      acc[a][c] -= F[c];
+      hs[c] -= F[c];
+    }
   }
 }
 
-// Line task t of phase ph (Section 5.1, along collapsed-coordinate lines, Remark 4): the
-// pairs of one eta_{ph+1}-line of N nodes, the facet nodes attached to it -- their
-// interface fluxes, facet-correction pairs and lift -- accumulated in registers.
-//   tetrahedra: phase 0 = eta1-lines + facets 2, 3; phase 1 = eta2-lines + facet 1;
-//               phase 2 = eta3-lines + facet 4;
-//   triangles:  phase 0 = eta1-lines + facets 2, 3; phase 1 = eta2-lines + facet 1.
-// A facet node of faces 1-3 couples only with the N volume nodes of its line, so its
-// h = B J f* - C^T 1 is complete inside the task and its lift R^T h (a 1D extrapolation
-// along the line) goes straight into the line's accumulators.  Facet-4 node (a1, b')
-// couples with all volume nodes (a1, ., .): task (a1, a2) writes h4 = B J f* of node
-// (a1, a2), then in N barrier-separated steps handles column b' = (a2 + k) mod N -- the
-// tasks sharing a1 update distinct facet nodes in every step -- and finally lifts
-// y = L2J h4 along its eta3-line.  Every thread of the block calls this (phase 2 has
-// barriers); `act` marks the threads that own a task.
-template <int D, int N, bool OTF = false>
-__device__ __forceinline__ void line_task(int ph, int t, bool act, const DevRef& R, const DevMesh& M, int64_t eg,
+// The same with the line's residuals in shared memory, r[c * Nq + base + a * stride]
+// (a loop over the line).
+template <int D, int N, class Dir>
+__device__ __forceinline__ void facet_strip_shared(const double* __restrict__ Sv, int Ntot, int base, int stride,
+                                                   const NodeState<D>& Sj, Dir&& dir, const FluxK& K, double* r,
+                                                   int Nq, double* hs) {
+#pragma unroll 1
+  for (int a = 0; a < N; ++a) {
+    const NodeState<D> Si = load_state<D>(Sv, Ntot, base + a * stride);
+    double nh[D], F[D + 2];
+    dir(a, nh);
+    ec_flux_fast<D>(Si, Sj, nh, K, F);
+#pragma unroll
+    for (int c = 0; c < D + 2; ++c) {
+      r[c * Nq + base + a * stride] -= F[c];
+      hs[c] -= F[c];
+    }
+  }
+}
+
+// The line task with the line's node residuals in the shared residual r (which the task
+// owns for its line in this phase) instead of registers; node a's running sum over its
+// pairs stays in registers.  Used by line_task for large N.
+template <int D, int N, bool OTF>
+__device__ __forceinline__ void line_task_shared(int ph, int t, bool act, const DevRef& R, const DevMesh& M, int64_t eg,
                                           const double* __restrict__ Sv, const double* __restrict__ Sf, double* r,
                                           double* h4, const double* __restrict__ vdir,
                                           const double* __restrict__ fdir, const FluxK& K) {
@@ -769,22 +772,11 @@ __device__ __forceinline__ void line_task(int ph, int t, bool act, const DevRef&
 #pragma unroll
       for (int c = 0; c < NC; ++c) acc[a][c] = 0.0;
   }
-  auto node_fma = [&](int a, int c, double x, double y) {   // residual(a, c) += x * y
-    if constexpr (SACC) {
-      double& ra = r[c * Nq + base + a * stride];
-      ra = fma(x, y, ra);
-    } else {
-      acc[a][c] = fma(x, y, acc[a][c]);
-    }
-  };
-  auto sub_flux = [&](int a, const double* F) {
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      if constexpr (SACC)
-        r[c * Nq + base + a * stride] -= F[c];
-      else
-        acc[a][c] -= F[c];
-    }
+  auto strip = [&](const NodeState<D>& Sj, auto&& dir, double* hs) {
+    if constexpr (SACC)
+      facet_strip_shared<D, N>(Sv, Ntot, base, stride, Sj, dir, K, r, Nq, hs);
+    else
+      facet_strip<D, N>(Sv, Ntot, base, stride, Sj, dir, K, acc, hs);
   };
   if (act) {
     constexpr int Lv = N * (N - 1) / 2;
@@ -852,21 +844,28 @@ __device__ __forceinline__ void line_task(int ph, int t, bool act, const DevRef&
           double jn[D];
           jn_at(f, jn);
           const double wq = 0.25 * R.wfac[f];
-          facet_strip<D, N, !SACC>(Sv, Ntot, base, stride, Sj, [&](int a, double* nh) {
+          strip(Sj, [&](int a, double* nh) {
             otf_fac_dir<D>(G, Nq, R.nhat[1 + zz], base + a * stride, jn, wq * l[a], nh);
-          }, K, sub_flux, hs);
+          }, hs);
         } else {
           const double* fd = fdir + R.fph_off[0] + (size_t)zz * N * D * T + t;
-          facet_strip<D, N, !SACC>(Sv, Ntot, base, stride, Sj, [&](int a, double* nh) {
+          strip(Sj, [&](int a, double* nh) {
 #pragma unroll
             for (int k = 0; k < D; ++k) nh[k] = fd[(a * D + k) * T];
-          }, K, sub_flux, hs);
+          }, hs);
         }
 #pragma unroll
         for (int a = 0; a < N; ++a) {
           const double la = l[a];
 #pragma unroll
-          for (int c = 0; c < NC; ++c) node_fma(a, c, -la, hs[c]);
+          for (int c = 0; c < NC; ++c) {
+          if constexpr (SACC) {
+            double& ra = r[c * Nq + base + a * stride];
+            ra = fma(-la, hs[c], ra);
+          } else {
+            acc[a][c] = fma(-la, hs[c], acc[a][c]);
+          }
+        }
         }
       }
     } else if (ph == 1) {
@@ -878,21 +877,28 @@ __device__ __forceinline__ void line_task(int ph, int t, bool act, const DevRef&
         double jn[D];
         jn_at(f, jn);
         const double wq = 0.25 * R.wfac[f];
-        facet_strip<D, N, !SACC>(Sv, Ntot, base, stride, Sj, [&](int a, double* nh) {
+        strip(Sj, [&](int a, double* nh) {
           otf_fac_dir<D>(G, Nq, R.nhat[0], base + a * stride, jn, wq * R.l2m[a], nh);
-        }, K, sub_flux, hs);
+        }, hs);
       } else {
         const double* fd = fdir + R.fph_off[1] + t;
-        facet_strip<D, N, !SACC>(Sv, Ntot, base, stride, Sj, [&](int a, double* nh) {
+        strip(Sj, [&](int a, double* nh) {
 #pragma unroll
           for (int k = 0; k < D; ++k) nh[k] = fd[(a * D + k) * T];
-        }, K, sub_flux, hs);
+        }, hs);
       }
 #pragma unroll
       for (int a = 0; a < N; ++a) {   // lift of facet 1 along the eta2-line
         const double la = R.l2m[a];
 #pragma unroll
-        for (int c = 0; c < NC; ++c) node_fma(a, c, -la, hs[c]);
+        for (int c = 0; c < NC; ++c) {
+          if constexpr (SACC) {
+            double& ra = r[c * Nq + base + a * stride];
+            ra = fma(-la, hs[c], ra);
+          } else {
+            acc[a][c] = fma(-la, hs[c], acc[a][c]);
+          }
+        }
       }
     } else if (D == 3) {
       double hs[NC];
@@ -917,15 +923,15 @@ __device__ __forceinline__ void line_task(int ph, int t, bool act, const DevRef&
           double jn[D];
           jn_at(3 * Nqf + j, jn);
           const double wq = 0.25 * R.wfac[3 * Nqf + j] * R.L2J[bp * N + a2];
-          facet_strip<D, N, !SACC>(Sv, Ntot, base, stride, Sj, [&](int a, double* nh) {
+          strip(Sj, [&](int a, double* nh) {
             otf_fac_dir<D>(G, Nq, R.nhat[3], base + a * stride, jn, wq * R.l3m[a], nh);
-          }, K, sub_flux, hs);
+          }, hs);
         } else {
           const double* fd = fd4 + (size_t)bp * N * D * T;
-          facet_strip<D, N, !SACC>(Sv, Ntot, base, stride, Sj, [&](int a, double* nh) {
+          strip(Sj, [&](int a, double* nh) {
 #pragma unroll
             for (int kk = 0; kk < D; ++kk) nh[kk] = fd[(a * D + kk) * T];
-          }, K, sub_flux, hs);
+          }, hs);
         }
 #pragma unroll
         for (int c = 0; c < NC; ++c) h4[c * Nqf + j] += hs[c];
@@ -946,7 +952,14 @@ __device__ __forceinline__ void line_task(int ph, int t, bool act, const DevRef&
       for (int a = 0; a < N; ++a) {
         const double la = R.l3m[a];
 #pragma unroll
-        for (int c = 0; c < NC; ++c) node_fma(a, c, -la, y[c]);
+        for (int c = 0; c < NC; ++c) {
+          if constexpr (SACC) {
+            double& ra = r[c * Nq + base + a * stride];
+            ra = fma(-la, y[c], ra);
+          } else {
+            acc[a][c] = fma(-la, y[c], acc[a][c]);
+          }
+        }
       }
     }
   }
@@ -957,6 +970,196 @@ __device__ __forceinline__ void line_task(int ph, int t, bool act, const DevRef&
 #pragma unroll
         for (int c = 0; c < NC; ++c) r[c * Nq + base + a * stride] += acc[a][c];
     }
+  }
+}
+
+// Line task t of phase ph (Section 5.1, along collapsed-coordinate lines, Remark 4): the
+// pairs of one eta_{ph+1}-line of N nodes, the facet nodes attached to it -- their
+// interface fluxes, facet-correction pairs and lift -- accumulated in registers.
+//   tetrahedra: phase 0 = eta1-lines + facets 2, 3; phase 1 = eta2-lines + facet 1;
+//               phase 2 = eta3-lines + facet 4;
+//   triangles:  phase 0 = eta1-lines + facets 2, 3; phase 1 = eta2-lines + facet 1.
+// A facet node of faces 1-3 couples only with the N volume nodes of its line, so its
+// h = B J f* - C^T 1 is complete inside the task and its lift R^T h (a 1D extrapolation
+// along the line) goes straight into the line's accumulators.  Facet-4 node (a1, b')
+// couples with all volume nodes (a1, ., .): task (a1, a2) writes h4 = B J f* of node
+// (a1, a2), then in N barrier-separated steps handles column b' = (a2 + k) mod N -- the
+// tasks sharing a1 update distinct facet nodes in every step -- and finally lifts
+// y = L2J h4 along its eta3-line.  Every thread of the block calls this (phase 2 has
+// barriers); `act` marks the threads that own a task.
+template <int D, int N, bool OTF = false>
+__device__ __forceinline__ void line_task(int ph, int t, bool act, const DevRef& R, const DevMesh& M, int64_t eg,
+                                          const double* __restrict__ Sv, const double* __restrict__ Sf, double* r,
+                                          double* h4, const double* __restrict__ vdir,
+                                          const double* __restrict__ fdir, const FluxK& K) {
+  constexpr int NC = D + 2;
+  // Where N accumulators no longer fit in registers beside the flux (tetrahedra N >= 6,
+  // triangles N >= 8) the line's residuals accumulate in shared memory instead.
+  if constexpr (D == 3 ? N >= 6 : N >= 8) {
+    line_task_shared<D, N, OTF>(ph, t, act, R, M, eg, Sv, Sf, r, h4, vdir, fdir, K);
+    return;
+  }
+  // on-the-fly directions: the element's metric terms and facet normals
+  const double* __restrict__ G = OTF ? M.gvol + eg * (int64_t)D * D * R.Nq : nullptr;
+  const double* __restrict__ JN = OTF ? M.jnf + eg * (int64_t)D * R.Nfn : nullptr;
+  auto jn_at = [&](int f, double* jn) {
+#pragma unroll
+    for (int m = 0; m < D; ++m) jn[m] = JN[m * R.Nfn + f];
+  };
+  const int Nq = R.Nq, Nfn = R.Nfn, Nqf = R.Nqf, T = R.T, Ntot = R.Ntot;
+  int base, stride;
+  if (D == 2) {
+    base = ph == 0 ? N * t : t;
+    stride = ph == 0 ? 1 : N;
+  } else {
+    if (ph == 0) { base = N * t; stride = 1; }
+    else if (ph == 1) { base = (t % N) + N * N * (t / N); stride = N; }
+    else { base = t; stride = N * N; }
+  }
+  double acc[N][NC];
+#pragma unroll
+  for (int a = 0; a < N; ++a)
+#pragma unroll
+    for (int c = 0; c < NC; ++c) acc[a][c] = 0.0;
+  if (act) {
+    constexpr int Lv = N * (N - 1) / 2;
+    const double* vd = vdir + (size_t)ph * Lv * D * T + t;
+#pragma unroll
+    for (int a = 0, m = 0; a < N; ++a) {
+#pragma unroll
+      for (int b = a + 1; b < N; ++b, ++m) {
+        const NodeState<D> Si = load_state<D>(Sv, Ntot, base + a * stride);
+        const NodeState<D> Sj = load_state<D>(Sv, Ntot, base + b * stride);
+        double nh[D], F[NC];
+        if constexpr (OTF) {
+          otf_vol_dir<D>(R, G, Nq, ph, a, b, base + a * stride, base + b * stride, nh);
+        } else {
+#pragma unroll
+          for (int k = 0; k < D; ++k) nh[k] = vd[(m * D + k) * T];
+        }
+        ec_flux_fast<D>(Si, Sj, nh, K, F);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          acc[a][c] -= F[c];
+          acc[b][c] += F[c];
+        }
+      }
+    }
+    if (ph == 0) {
+#pragma unroll
+      for (int zz = 0; zz < 2; ++zz) {
+        const int f = (1 + zz) * Nqf + t;
+        double hs[NC];
+        interface_flux<D>(M, Nq, Nfn, Ntot, eg, f, Sf, K, hs);
+        const NodeState<D> Sj = load_state<D>(Sf, Ntot, f);
+        const double* l = zz == 0 ? R.l1p : R.l1m;   // R entries along the eta1-line (and the lift)
+        if constexpr (OTF) {
+          double jn[D];
+          jn_at(f, jn);
+          const double wq = 0.25 * R.wfac[f];
+          facet_strip<D, N>(Sv, Ntot, base, stride, Sj, [&](int a, double* nh) {
+            otf_fac_dir<D>(G, Nq, R.nhat[1 + zz], base + a * stride, jn, wq * l[a], nh);
+          }, K, acc, hs);
+        } else {
+          const double* fd = fdir + R.fph_off[0] + (size_t)zz * N * D * T + t;
+          facet_strip<D, N>(Sv, Ntot, base, stride, Sj, [&](int a, double* nh) {
+#pragma unroll
+            for (int k = 0; k < D; ++k) nh[k] = fd[(a * D + k) * T];
+          }, K, acc, hs);
+        }
+#pragma unroll
+        for (int a = 0; a < N; ++a) {
+          const double la = l[a];
+#pragma unroll
+          for (int c = 0; c < NC; ++c) acc[a][c] = fma(-la, hs[c], acc[a][c]);
+        }
+      }
+    } else if (ph == 1) {
+      const int f = t;
+      double hs[NC];
+      interface_flux<D>(M, Nq, Nfn, Ntot, eg, f, Sf, K, hs);
+      const NodeState<D> Sj = load_state<D>(Sf, Ntot, f);
+      if constexpr (OTF) {
+        double jn[D];
+        jn_at(f, jn);
+        const double wq = 0.25 * R.wfac[f];
+        facet_strip<D, N>(Sv, Ntot, base, stride, Sj, [&](int a, double* nh) {
+          otf_fac_dir<D>(G, Nq, R.nhat[0], base + a * stride, jn, wq * R.l2m[a], nh);
+        }, K, acc, hs);
+      } else {
+        const double* fd = fdir + R.fph_off[1] + t;
+        facet_strip<D, N>(Sv, Ntot, base, stride, Sj, [&](int a, double* nh) {
+#pragma unroll
+          for (int k = 0; k < D; ++k) nh[k] = fd[(a * D + k) * T];
+        }, K, acc, hs);
+      }
+#pragma unroll
+      for (int a = 0; a < N; ++a) {   // lift of facet 1 along the eta2-line
+        const double la = R.l2m[a];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) acc[a][c] = fma(-la, hs[c], acc[a][c]);
+      }
+    } else if (D == 3) {
+      double hs[NC];
+      interface_flux<D>(M, Nq, Nfn, Ntot, eg, 3 * Nqf + t, Sf, K, hs);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) h4[c * Nqf + t] = hs[c];
+    }
+  }
+  if (D == 3 && ph == 2) {
+    const int a1 = t % N, a2 = t / N;
+    const double* fd4 = (act && !OTF) ? fdir + R.fph_off[3] + t : nullptr;
+#pragma unroll 1
+    for (int k = 0; k < N; ++k) {
+      if (act) {
+        const int bp = a2 + k < N ? a2 + k : a2 + k - N;
+        const int j = a1 + N * bp;
+        const NodeState<D> Sj = load_state<D>(Sf, Ntot, 3 * Nqf + j);
+        double hs[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) hs[c] = 0.0;
+        if constexpr (OTF) {
+          double jn[D];
+          jn_at(3 * Nqf + j, jn);
+          const double wq = 0.25 * R.wfac[3 * Nqf + j] * R.L2J[bp * N + a2];
+          facet_strip<D, N>(Sv, Ntot, base, stride, Sj, [&](int a, double* nh) {
+            otf_fac_dir<D>(G, Nq, R.nhat[3], base + a * stride, jn, wq * R.l3m[a], nh);
+          }, K, acc, hs);
+        } else {
+          const double* fd = fd4 + (size_t)bp * N * D * T;
+          facet_strip<D, N>(Sv, Ntot, base, stride, Sj, [&](int a, double* nh) {
+#pragma unroll
+            for (int kk = 0; kk < D; ++kk) nh[kk] = fd[(a * D + kk) * T];
+          }, K, acc, hs);
+        }
+#pragma unroll
+        for (int c = 0; c < NC; ++c) h4[c * Nqf + j] += hs[c];
+      }
+      __syncthreads();
+    }
+    if (act) {   // lift of facet 4: y = sum_b' L2J[b'][a2] h4(a1, b'), along the eta3-line
+      double y[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) y[c] = 0.0;
+#pragma unroll 1
+      for (int bp = 0; bp < N; ++bp) {
+        const double w = R.L2J[bp * N + a2];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) y[c] = fma(w, h4[c * Nqf + a1 + N * bp], y[c]);
+      }
+#pragma unroll
+      for (int a = 0; a < N; ++a) {
+        const double la = R.l3m[a];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) acc[a][c] = fma(-la, y[c], acc[a][c]);
+      }
+    }
+  }
+  if (act) {
+#pragma unroll
+    for (int a = 0; a < N; ++a)
+#pragma unroll
+      for (int c = 0; c < NC; ++c) r[c * Nq + base + a * stride] += acc[a][c];
   }
 }
 
