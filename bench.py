@@ -211,6 +211,13 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def profiled_range(torch, on):
+    """Opens (on) or closes the launch range that `ncu --profile-from-start off` captures:
+    the timed RK4 steps and the timed VJP calls.  Without a profiler attached it has no
+    effect."""
+    (torch.cuda.profiler.start if on else torch.cuda.profiler.stop)()
+
+
 def run_ours(args):
     import torch
     import paper_2312_07874_gb300 as E
@@ -252,10 +259,12 @@ def run_ours(args):
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with torch.cuda.stream(stream):
+        profiled_range(torch, True)
         ev0.record(stream)
         for _ in range(args.steps):
             gm.rk_step(u, dt)
         ev1.record(stream)
+        profiled_range(torch, False)
     stream.synchronize()
     barrier()
     torch.cuda.synchronize()
@@ -296,10 +305,12 @@ def run_ours(args):
             E.esd_rhs(gm.handle, u, out, stream)
         f1.record(stream)
         g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        profiled_range(torch, True)
         g0.record(stream)
         for _ in range(nrep):
             E.esd_rhs_vjp(gm.handle, u, cot, grad, stream)
         g1.record(stream)
+        profiled_range(torch, False)
     stream.synchronize()
     fwd_ms = f0.elapsed_time(f1) / nrep
     adj_ms = g0.elapsed_time(g1) / nrep
