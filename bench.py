@@ -314,6 +314,26 @@ def run_ours(args):
     stream.synchronize()
     fwd_ms = f0.elapsed_time(f1) / nrep
     adj_ms = g0.elapsed_time(g1) / nrep
+    # reverse mode with the forward's tape kept (esd_rhs_save) and read by the VJP
+    # (esd_rhs_vjp_saved): the adjoint does not recompute the entropy projection
+    tape = gm.empty_tapes()
+    with torch.cuda.stream(stream):
+        E.esd_rhs_save(gm.handle, u, out, tape, stream)
+        E.esd_rhs_vjp_saved(gm.handle, u, tape, cot, grad, stream)
+        h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        h0.record(stream)
+        for _ in range(nrep):
+            E.esd_rhs_save(gm.handle, u, out, tape, stream)
+        h1.record(stream)
+        k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k0.record(stream)
+        for _ in range(nrep):
+            E.esd_rhs_vjp_saved(gm.handle, u, tape, cot, grad, stream)
+        k1.record(stream)
+    stream.synchronize()
+    fwd_save_ms = h0.elapsed_time(h1) / nrep
+    adj_saved_ms = k0.elapsed_time(k1) / nrep
+    del tape
     rflops, npairs = residual_kernel_flops(D, p)
     achieved = rflops * nE / (res_ms * 1e-3)
     peak = E.esd_measure_fp64_peak(stream)
@@ -372,7 +392,11 @@ def run_ours(args):
         "two_point_fluxes_per_s": 4.0 * npairs * nE * world / (ms * 1e-3),
         "paper_flux_count_equivalent_per_s": 4.0 * info["paper_flux_count_per_elem"] * nE * world / (ms * 1e-3),
         "adjoint_forward_ratio": adj_ms / fwd_ms,
-        "adjoint": {"rhs_ms": fwd_ms, "rhs_vjp_ms": adj_ms},
+        "adjoint_forward_ratio_saved_tape": adj_saved_ms / fwd_save_ms,
+        "adjoint": {"rhs_ms": fwd_ms, "rhs_vjp_ms": adj_ms, "rhs_save_ms": fwd_save_ms,
+                    "rhs_vjp_saved_ms": adj_saved_ms,
+                    "note": "adjoint_forward_ratio: esd_rhs_vjp (recomputes the entropy projection) / esd_rhs; "
+                            "_saved_tape: esd_rhs_vjp_saved (reads the forward's tape) / esd_rhs_save"},
         "e2e": {"value": 4.0 * dof * world / (e2e_ms * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
         "gpu_launches": 8 * args.steps,
@@ -732,22 +756,33 @@ def run_sweep(args):
     out, grad = torch.empty_like(u), torch.empty_like(u)
     fwd = _time_flushed(torch, stream, lambda: E.esd_rhs(gm.handle, u, out, stream), reps, flush)
     adj = _time_flushed(torch, stream, lambda: E.esd_rhs_vjp(gm.handle, u, cot, grad, stream), reps, flush)
+    tape = gm.empty_tapes()
+    fwd_s = _time_flushed(torch, stream, lambda: E.esd_rhs_save(gm.handle, u, out, tape, stream), reps, flush)
+    adj_s = _time_flushed(torch, stream, lambda: E.esd_rhs_vjp_saved(gm.handle, u, tape, cot, grad, stream),
+                          reps, flush)
     lam = I.max_wave_speed_sampled(lambda y: I.taylor_green(y, 0.1), 3, 2 * np.pi)
     dt = 0.1 * (2 * np.pi / 8) / (lam * 7)
 
-    def fwd_only():
+    def fwd_only(mode):
         with torch.no_grad():
-            rollout(u, gm, dt, 20, "stages")
+            rollout(u, gm, dt, 20, mode)
 
-    def fwd_bwd():
+    def fwd_bwd(mode):
         u0 = u.clone().requires_grad_(True)
-        (cot * rollout(u0, gm, dt, 20, "stages")).sum().backward()
-    t_f = _time_flushed(torch, stream, fwd_only, 2, flush)
-    t_fb = _time_flushed(torch, stream, fwd_bwd, 2, flush)
+        (cot * rollout(u0, gm, dt, 20, mode)).sum().backward()
+    roll = {}
+    for mode in ("stages", "tapes"):
+        t_f = _time_flushed(torch, stream, lambda: fwd_only(mode), 2, flush)
+        t_fb = _time_flushed(torch, stream, lambda: fwd_bwd(mode), 2, flush)
+        roll[mode] = {"rollout_20_steps_ms": t_f, "rollout_20_steps_forward_backward_ms": t_fb,
+                      "rollout_backward_forward_ratio": (t_fb - t_f) / t_f}
     print(json.dumps({"kind": "sweep", "workload": "vjp tet_tgv_curved p=3 (8^3 x 6 = 3072 tets, TGV + N(0,1e-3))",
                       "rhs_ms": fwd, "rhs_vjp_ms": adj, "adjoint_forward_ratio": adj / fwd,
-                      "rollout_20_steps_ms": t_f, "rollout_20_steps_forward_backward_ms": t_fb,
-                      "rollout_backward_forward_ratio": (t_fb - t_f) / t_f, "checkpoint": "stages",
+                      "rhs_save_ms": fwd_s, "rhs_vjp_saved_ms": adj_s, "adjoint_forward_ratio_saved_tape": adj_s / fwd_s,
+                      "rollout_20_steps_ms": roll["stages"]["rollout_20_steps_ms"],
+                      "rollout_20_steps_forward_backward_ms": roll["stages"]["rollout_20_steps_forward_backward_ms"],
+                      "rollout_backward_forward_ratio": roll["stages"]["rollout_backward_forward_ratio"],
+                      "checkpoint": "stages", "rollout_checkpoint_tapes": roll["tapes"],
                       "l2": "flushed (256 MB write) before every timed call", "dtype": "f64"}), flush=True)
 
 

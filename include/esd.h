@@ -126,7 +126,8 @@ esd_status esd_mesh_destroy(esd_mesh mesh);
 esd_status esd_mesh_info(esd_mesh mesh, esd_info* out);
 
 /* Synchronize the stream, then report (and clear) the device error flag: ESD_OK,
- * ESD_ERR_TIMEOUT or ESD_ERR_STATE (a non-admissible state).
+ * ESD_ERR_TIMEOUT, ESD_ERR_STATE (a non-admissible state) or ESD_ERR_ARG (an
+ * esd_part_export element index outside the partition).
  * ESD_ERR_TIMEOUT means that a shared-memory staging copy of some block did not complete
  * within its bounded wait of about one second: that block skipped its work (its outputs
  * hold stale values) after waiting once more, for the same time, for its copies to land.
@@ -196,6 +197,41 @@ esd_status esd_rk_step(esd_mesh mesh, double* u, double dt, double* stage_ckpt, 
 esd_status esd_rk_step_vjp(esd_mesh mesh, const double* stage_ckpt, double dt, const double* cot_out,
                            double* cot_in, void* stream);
 
+/* Reverse mode with a saved forward pass.  esd_rhs_vjp and esd_rk_step_vjp first recompute
+ * the entropy projection of their input state (Eq. (entropy_expansion) and the states
+ * U(w) at every volume and facet node), which the adjoint kernels read.  A caller that can
+ * hold those per-node states from the forward call skips that work: the _save calls run
+ * the same kernels as esd_rhs / esd_rk_step but leave the projection of each right-hand
+ * side in a caller-owned tape, and the _saved VJPs read it instead of recomputing it.
+ * Results are identical (bitwise) to the recomputing calls.
+ *
+ * A tape holds esd_tape_doubles() doubles: the entropy-projected states with their
+ * derived fields [n_elem][dim+5][N_q + N_f N_fq] and the facet sound speeds [n_elem][N_f N_fq],
+ * each padded to a multiple of 32 doubles (about 15 KB per tetrahedron at p = 4, 11 times
+ * the modal state).  tape / tapes: device, 16-byte aligned (ESD_ERR_ARG otherwise: the
+ * kernels stage each element's states with bulk copies), owned by the caller.  A tape is
+ * valid for the state it was written from until it is overwritten; the library cannot
+ * check that the u passed to a _saved VJP is that state.  Meshes created with
+ * ESD_MESH_METRICS_ON_THE_FLY have no VJP (ESD_ERR_UNSUPPORTED). */
+esd_status esd_tape_doubles(esd_mesh mesh, int64_t* n_doubles);
+
+/* esd_rhs, keeping the forward tape of u in tape (esd_tape_doubles doubles). */
+esd_status esd_rhs_save(esd_mesh mesh, const double* u, double* dudt, double* tape, void* stream);
+
+/* esd_rhs_vjp at the state u whose tape esd_rhs_save wrote (the projection is not
+ * recomputed).  u, cot, grad as for esd_rhs_vjp; tape is only read. */
+esd_status esd_rhs_vjp_saved(esd_mesh mesh, const double* u, const double* tape, const double* cot, double* grad,
+                             void* stream);
+
+/* esd_rk_step with stage_ckpt (required here) and the four stages' forward tapes in
+ * tapes: device [4][esd_tape_doubles].  Graph-replayed like esd_rk_step; the graph cache
+ * key includes tapes. */
+esd_status esd_rk_step_save(esd_mesh mesh, double* u, double dt, double* stage_ckpt, double* tapes, void* stream);
+
+/* esd_rk_step_vjp reading the tapes that esd_rk_step_save wrote with the same stage_ckpt. */
+esd_status esd_rk_step_vjp_saved(esd_mesh mesh, const double* stage_ckpt, const double* tapes, double dt,
+                                 const double* cot_out, double* cot_in, void* stream);
+
 /* Diagnostics of Theorems 2 and 4: out (device, N_c + 2 doubles) receives
  * sum_kappa 1^T r^(kappa,e) for each variable e (equal to sum 1^T W J V d u~/dt), then
  * sum_kappa sum_e w^T r (the entropy rate, zero for ESD_FLUX_EC on periodic meshes), then
@@ -210,6 +246,56 @@ esd_status esd_diagnostics(esd_mesh mesh, const double* u, double* out, void* st
  * integration error, non-increasing for ESD_FLUX_LF).  Quadrature of the mass matrix
  * (interpolated J).  Used for conservation and entropy time series over a run. */
 esd_status esd_integrals(esd_mesh mesh, const double* u, double* out, void* stream);
+
+/* Element partitions.  The semi-discretisation couples elements only through the interface
+ * flux of Eq. (num_flux) at shared facets (Section 4.3), i.e. through the neighbours' facet
+ * traces, so a mesh split into partitions needs one exchange of facet traces per right-hand
+ * side (and, for the VJP, one exchange of the interface cotangents).  These calls expose
+ * that structure: each partition is a mesh of its own, the phases of the evaluation are
+ * separate calls, and the traces travel in caller-owned device buffers between them (on
+ * several GPUs a collective or peer copy moves them; on one GPU a plain buffer does).
+ *
+ * esd_part_create: desc describes n_elem = n_local + n_ghost elements, the n_ghost ghosts
+ * last, with their map nodes.  Local elements are computed; ghosts are not and exist only
+ * to supply traces.  A local element's facet may face a ghost (nbr_elem in [n_local,
+ * n_elem)); that ghost's nbr_elem / nbr_face entry for the shared facet must point back.
+ * Other ghost facets are not read and may hold any value.  Facet nodes are matched as for
+ * esd_mesh_create.  u, dudt, grad of a partition are [n_local][N_c][N_p*].  n_ghost = 0
+ * gives an ordinary mesh.
+ *
+ * Calls that evaluate a whole right-hand side at once (esd_rhs, esd_rhs_save,
+ * esd_rhs_static_scratch, esd_rk_step*, esd_rhs_vjp*, esd_rk_step_vjp*, esd_diagnostics,
+ * esd_batch_create) return ESD_ERR_UNSUPPORTED on a partition with ghosts.  Instead:
+ *   d u~/dt:  esd_rhs_begin(u)  (entropy projection, Eq. (entropy_expansion), of the local
+ *             elements) -> esd_part_export(ESD_TRACE_STATES) of the elements the other
+ *             partitions hold as ghosts, esd_part_import(ESD_TRACE_STATES) of this
+ *             partition's ghosts -> esd_rhs_end(dudt)  (Eq. (dudt_modal));
+ *   VJP:      esd_rhs_begin(u) -> exchange ESD_TRACE_STATES -> esd_rhs_vjp_mid(cot) ->
+ *             exchange ESD_TRACE_COTANGENTS -> esd_rhs_vjp_end(u, grad).
+ * Each partition's result equals the unpartitioned call's rows for its elements bit for
+ * bit.  The phases also work on ordinary meshes (no exchange needed).  The mesh workspace
+ * carries the state between phases: one evaluation at a time per mesh.
+ *
+ * esd_part_info: n_ghost, and the doubles per element of a trace message:
+ *   ESD_TRACE_STATES      (dim + 6) N_f N_fq: the entropy-projected states with their
+ *                         derived fields at the facet nodes, then the facet sound speeds;
+ *   ESD_TRACE_COTANGENTS  (dim + 2) N_f N_fq: the cotangents of the neighbour's facet states
+ *                         produced by the residual adjoint.
+ * esd_part_export: elems (device int64 [n]) are local element indices; buf (device
+ * [n][trace doubles]) receives their messages in that order.  An index outside [0, n_local)
+ * sends zeros and makes the next esd_mesh_check return ESD_ERR_ARG.
+ * esd_part_import: buf (device [n][trace doubles]) fills ghosts first .. first + n - 1
+ * (ghost g is element n_local + g of the descriptor); ESD_ERR_ARG if the range leaves
+ * [0, n_ghost).  Buffers must not overlap the mesh's own memory. */
+enum { ESD_TRACE_STATES = 0, ESD_TRACE_COTANGENTS = 1 };
+esd_status esd_part_create(const esd_mesh_desc* desc, int64_t n_ghost, esd_mesh* out);
+esd_status esd_part_info(esd_mesh mesh, int64_t* n_ghost, int64_t* trace_doubles, int64_t* cotangent_doubles);
+esd_status esd_rhs_begin(esd_mesh mesh, const double* u, void* stream);
+esd_status esd_rhs_end(esd_mesh mesh, double* dudt, void* stream);
+esd_status esd_rhs_vjp_mid(esd_mesh mesh, const double* cot, void* stream);
+esd_status esd_rhs_vjp_end(esd_mesh mesh, const double* u, double* grad, void* stream);
+esd_status esd_part_export(esd_mesh mesh, int kind, const int64_t* elems, int64_t n, double* buf, void* stream);
+esd_status esd_part_import(esd_mesh mesh, int kind, const double* buf, int64_t first, int64_t n, void* stream);
 
 /* The skew-symmetric nodal form of Section 4.4, Eq. (rhs_skew), with the modal update of
  * Eq. (modal) through the weight-adjusted inverse (M = I):

@@ -61,6 +61,24 @@ SYMBOLS = {
     "esd_rk_step": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
     "esd_rk_step_vjp": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
                          ctypes.c_void_p], ctypes.c_int),
+    "esd_tape_doubles": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+    "esd_rhs_save": ([ctypes.c_void_p] * 5, ctypes.c_int),
+    "esd_rhs_vjp_saved": ([ctypes.c_void_p] * 6, ctypes.c_int),
+    "esd_rk_step_save": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
+                          ctypes.c_void_p], ctypes.c_int),
+    "esd_rk_step_vjp_saved": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p,
+                               ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "esd_part_create": ([ctypes.POINTER(esd_mesh_desc), ctypes.c_int64, ctypes.POINTER(ctypes.c_void_p)],
+                        ctypes.c_int),
+    "esd_part_info": ([ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_int64)] * 3, ctypes.c_int),
+    "esd_rhs_begin": ([ctypes.c_void_p] * 3, ctypes.c_int),
+    "esd_rhs_end": ([ctypes.c_void_p] * 3, ctypes.c_int),
+    "esd_rhs_vjp_mid": ([ctypes.c_void_p] * 3, ctypes.c_int),
+    "esd_rhs_vjp_end": ([ctypes.c_void_p] * 4, ctypes.c_int),
+    "esd_part_export": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                         ctypes.c_void_p], ctypes.c_int),
+    "esd_part_import": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                         ctypes.c_void_p], ctypes.c_int),
     "esd_diagnostics": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
     "esd_integrals": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
     "esd_batch_create": ([ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
@@ -137,7 +155,7 @@ ESD_MESH_PAIR_TABLES, ESD_MESH_METRICS_ON_THE_FLY = 0, 1
 
 
 def esd_mesh_create(dim, p, map_nodes, nbr_elem, nbr_face, gamma=1.4, flux=ESD_FLUX_LF,
-                    options=ESD_MESH_PAIR_TABLES):
+                    options=ESD_MESH_PAIR_TABLES, n_ghost=0):
     X = np.ascontiguousarray(map_nodes, dtype=np.float64)
     ne = np.ascontiguousarray(nbr_elem, dtype=np.int32)
     nf = np.ascontiguousarray(nbr_face, dtype=np.int8)
@@ -145,7 +163,11 @@ def esd_mesh_create(dim, p, map_nodes, nbr_elem, nbr_face, gamma=1.4, flux=ESD_F
                       ne.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), nf.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)),
                       gamma, flux)
     h = ctypes.c_void_p()
-    if options == ESD_MESH_PAIR_TABLES:
+    if n_ghost:
+        if options != ESD_MESH_PAIR_TABLES:
+            raise ValueError("partition meshes use the stored pair tables")
+        _check(lib().esd_part_create(ctypes.byref(d), int(n_ghost), ctypes.byref(h)))
+    elif options == ESD_MESH_PAIR_TABLES:
         _check(lib().esd_mesh_create(ctypes.byref(d), ctypes.byref(h)))
     else:
         _check(lib().esd_mesh_create_ex(ctypes.byref(d), int(options), ctypes.byref(h)))
@@ -229,6 +251,72 @@ def esd_rk_step_vjp(h, stage_ckpt, dt, cot_out, cot_in, stream=None):
     _check(lib().esd_rk_step_vjp(h, _ptr(stage_ckpt), float(dt), _ptr(cot_out), _ptr(cot_in), _stream(stream)))
 
 
+def esd_tape_doubles(h):
+    """Doubles of one forward tape (the entropy-projected states of one right-hand side)."""
+    n = ctypes.c_int64()
+    _check(lib().esd_tape_doubles(h, ctypes.byref(n)))
+    return n.value
+
+
+def esd_rhs_save(h, u, dudt, tape, stream=None):
+    _check(lib().esd_rhs_save(h, _ptr(u), _ptr(dudt), _ptr(tape), _stream(stream)))
+
+
+def esd_rhs_vjp_saved(h, u, tape, cot, grad, stream=None):
+    _check(lib().esd_rhs_vjp_saved(h, _ptr(u), _ptr(tape), _ptr(cot), _ptr(grad), _stream(stream)))
+
+
+def esd_rk_step_save(h, u, dt, stage_ckpt, tapes, stream=None):
+    _check(lib().esd_rk_step_save(h, _ptr(u), float(dt), _ptr(stage_ckpt), _ptr(tapes), _stream(stream)))
+
+
+def esd_rk_step_vjp_saved(h, stage_ckpt, tapes, dt, cot_out, cot_in, stream=None):
+    _check(lib().esd_rk_step_vjp_saved(h, _ptr(stage_ckpt), _ptr(tapes), float(dt), _ptr(cot_out), _ptr(cot_in),
+                                       _stream(stream)))
+
+
+ESD_TRACE_STATES, ESD_TRACE_COTANGENTS = 0, 1
+
+
+def esd_part_info(h):
+    """(n_ghost, doubles per element of a state trace, of a cotangent trace)."""
+    a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().esd_part_info(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value
+
+
+def esd_rhs_begin(h, u, stream=None):
+    _check(lib().esd_rhs_begin(h, _ptr(u), _stream(stream)))
+
+
+def esd_rhs_end(h, dudt, stream=None):
+    _check(lib().esd_rhs_end(h, _ptr(dudt), _stream(stream)))
+
+
+def esd_rhs_vjp_mid(h, cot, stream=None):
+    _check(lib().esd_rhs_vjp_mid(h, _ptr(cot), _stream(stream)))
+
+
+def esd_rhs_vjp_end(h, u, grad, stream=None):
+    _check(lib().esd_rhs_vjp_end(h, _ptr(u), _ptr(grad), _stream(stream)))
+
+
+def _ptr_i64(t):
+    """Device pointer of a contiguous int64 CUDA tensor."""
+    import torch
+    if t.dtype != torch.int64 or not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous int64 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def esd_part_export(h, kind, elems, buf, stream=None):
+    _check(lib().esd_part_export(h, int(kind), _ptr_i64(elems), elems.numel(), _ptr(buf), _stream(stream)))
+
+
+def esd_part_import(h, kind, buf, first, n, stream=None):
+    _check(lib().esd_part_import(h, int(kind), _ptr(buf), int(first), int(n), _stream(stream)))
+
+
 def esd_diagnostics(h, u, out, stream=None):
     _check(lib().esd_diagnostics(h, _ptr(u), _ptr(out), _stream(stream)))
 
@@ -301,10 +389,14 @@ def esd_batch_rk_step(b, us, dts, stream=None):
 class Mesh:
     """Owns an esd_mesh handle; state tensors are float64 CUDA [n_elem, N_c, N_p*]."""
 
-    def __init__(self, dim, p, map_nodes, nbr_elem, nbr_face, gamma=1.4, flux="LF", metrics_on_the_fly=False):
+    def __init__(self, dim, p, map_nodes, nbr_elem, nbr_face, gamma=1.4, flux="LF", metrics_on_the_fly=False,
+                 n_ghost=0):
+        """n_ghost > 0: a partition mesh whose last n_ghost elements are ghosts
+        (esd_part_create; paper_2312_07874_gb300.partition builds the descriptions)."""
         self.handle = esd_mesh_create(dim, p, map_nodes, nbr_elem, nbr_face, gamma,
                                       ESD_FLUX_LF if flux == "LF" else ESD_FLUX_EC,
-                                      ESD_MESH_METRICS_ON_THE_FLY if metrics_on_the_fly else ESD_MESH_PAIR_TABLES)
+                                      ESD_MESH_METRICS_ON_THE_FLY if metrics_on_the_fly else ESD_MESH_PAIR_TABLES,
+                                      n_ghost)
         self.info = esd_mesh_info(self.handle)
         self.dim, self.p = dim, p
         self.n_elem = self.info["n_elem"]
@@ -326,6 +418,13 @@ class Mesh:
     def empty_state(self):
         import torch
         return torch.empty((self.n_elem, self.nc, self.n_modes), dtype=torch.float64, device="cuda")
+
+    def empty_tapes(self, *shape):
+        """Forward tapes (esd_rhs_save / esd_rk_step_save): a float64 tensor of shape
+        shape + (esd_tape_doubles,) on the device; torch allocations are 256-byte aligned and
+        each tape is a multiple of 32 doubles, so every tape in it is 16-byte aligned."""
+        import torch
+        return torch.empty(tuple(shape) + (esd_tape_doubles(self.handle),), dtype=torch.float64, device="cuda")
 
     def volume_nodes(self):
         return esd_mesh_volume_nodes(self.handle, self.n_elem, self.n_q, self.dim)

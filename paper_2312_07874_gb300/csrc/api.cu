@@ -81,6 +81,7 @@ struct GraphEntry {
   double* u;
   double dt;
   double* ckpt;
+  double* tapes;   // esd_rk_step_save: the four stages' forward tapes (else null)
   cudaStream_t s;
   cudaGraphExec_t exec;
 };
@@ -89,6 +90,7 @@ struct esd_mesh_s {
   int dim = 0, p = 0, nc = 0;
   int device = -1;             // the device current at esd_mesh_create; it owns every allocation
   int64_t E = 0;
+  int64_t n_ghost = 0;         // partition meshes (esd_part_create): ghost elements after the E local ones
   RefTables ref;
   std::vector<double> xvol;
   DevRef R{};
@@ -153,7 +155,7 @@ const char* esd_status_string(esd_status s) {
 
 const char* esd_last_error(void) { return g_err.c_str(); }
 
-static esd_status mesh_create(const esd_mesh_desc* d, int tables, esd_mesh* out);
+static esd_status mesh_create(const esd_mesh_desc* d, int tables, esd_mesh* out, int64_t n_ghost = 0);
 
 esd_status esd_mesh_create(const esd_mesh_desc* d, esd_mesh* out) {
   ESD_RANGE("esd_mesh_create");
@@ -168,9 +170,17 @@ esd_status esd_mesh_create_ex(const esd_mesh_desc* d, int options, esd_mesh* out
   return fail(ESD_ERR_ARG, "options must be ESD_MESH_PAIR_TABLES or ESD_MESH_METRICS_ON_THE_FLY");
 }
 
+// Calls that evaluate a whole right-hand side in one go need every neighbour's trace; on a
+// partition mesh the ghosts' traces arrive between the phases (esd_rhs_begin ... esd_rhs_end).
+static esd_status reject_partition(const esd_mesh_s* m, const char* call) {
+  if (m->n_ghost == 0) return ESD_OK;
+  return fail(ESD_ERR_UNSUPPORTED, std::string(call) + " on a partition mesh: use esd_rhs_begin, esd_part_export / "
+                                   "esd_part_import and esd_rhs_end (esd_rhs_vjp_mid / esd_rhs_vjp_end for the VJP)");
+}
+
 // Mesh creation with the chosen pair tables (entropy-stable pair directions, or the
 // skew-symmetric form's line-pair coefficients for esd_skew_create).
-static esd_status mesh_create(const esd_mesh_desc* d, int tables, esd_mesh* out) {
+static esd_status mesh_create(const esd_mesh_desc* d, int tables, esd_mesh* out, int64_t n_ghost) {
   if (!d || !out) return fail(ESD_ERR_ARG, "null descriptor or output");
   *out = nullptr;
   if (d->dim != 2 && d->dim != 3) return fail(ESD_ERR_ARG, "dim must be 2 or 3");
@@ -180,7 +190,7 @@ static esd_status mesh_create(const esd_mesh_desc* d, int tables, esd_mesh* out)
   if (d->flux != ESD_FLUX_EC && d->flux != ESD_FLUX_LF) return fail(ESD_ERR_ARG, "flux must be ESD_FLUX_EC or ESD_FLUX_LF");
   HostMesh H;
   std::string err;
-  esd_status st = build_host_mesh(*d, &H, &err, tables);
+  esd_status st = build_host_mesh(*d, &H, &err, tables, n_ghost);
   if (st != ESD_OK) return fail(st, err);
   int device = -1;
   cudaError_t de = cudaGetDevice(&device);
@@ -190,7 +200,8 @@ static esd_status mesh_create(const esd_mesh_desc* d, int tables, esd_mesh* out)
   m->dim = d->dim;
   m->p = d->p;
   m->nc = d->dim + 2;
-  m->E = d->n_elem;
+  m->E = d->n_elem - n_ghost;
+  m->n_ghost = n_ghost;
   m->ref = H.ref;
   m->xvol = std::move(H.xvol);
   const RefTables& r = m->ref;
@@ -273,9 +284,12 @@ static esd_status mesh_create(const esd_mesh_desc* d, int tables, esd_mesh* out)
     }
     M.minv = mi;
   }
-  const size_t nstate = (size_t)m->E * nfields(r.dim) * r.Ntot;
+  // per-node states and facet sound speeds: rows for the local elements, then (partition
+  // meshes) the ghosts' rows, written by esd_part_import
+  const int64_t Erow = m->E + n_ghost;
+  const size_t nstate = (size_t)Erow * nfields(r.dim) * r.Ntot;
   const size_t nmodal = (size_t)m->E * m->nc * r.Np;
-  if ((st = m->alloc(&M.states, nstate)) || (st = m->alloc(&M.cfac, (size_t)m->E * r.Nfn)) ||
+  if ((st = m->alloc(&M.states, nstate)) || (st = m->alloc(&M.cfac, (size_t)Erow * r.Nfn)) ||
       (st = m->alloc(&M.flag, 1)) || (st = m->alloc(&m->ws_acc, nmodal)) || (st = m->alloc(&m->ws_stage, nmodal)) ||
       (st = m->alloc(&m->ws_diag, (size_t)m->E * (m->nc + 2)))) {
     delete m;
@@ -284,13 +298,18 @@ static esd_status mesh_create(const esd_mesh_desc* d, int tables, esd_mesh* out)
   // the VJP's workspaces, only where the VJP can run (meshes with the stored pair tables)
   if ((tables & kTablesEntropyStable) &&
       ((st = m->alloc(&m->ws_qbar, (size_t)m->E * m->nc * r.Ntot)) ||
-       (st = m->alloc(&m->ws_qext, (size_t)m->E * m->nc * r.Nfn)) || (st = m->alloc(&m->ws_adj[0], nmodal)) ||
+       (st = m->alloc(&m->ws_qext, (size_t)Erow * m->nc * r.Nfn)) || (st = m->alloc(&m->ws_adj[0], nmodal)) ||
        (st = m->alloc(&m->ws_adj[1], nmodal)) || (st = m->alloc(&m->ws_adj[2], nmodal)) ||
        (st = m->alloc(&m->ws_adj[3], nmodal)))) {
     delete m;
     return st;
   }
   cudaMemset(M.flag, 0, sizeof(int));
+  if (n_ghost > 0) {   // defined values in the ghost rows until the first import
+    cudaMemset(M.states, 0, nstate * sizeof(double));
+    cudaMemset(M.cfac, 0, (size_t)Erow * r.Nfn * sizeof(double));
+    if (m->ws_qext) cudaMemset(m->ws_qext, 0, (size_t)Erow * m->nc * r.Nfn * sizeof(double));
+  }
   m->L = choose_launch(r);
   cudaError_t e = set_smem_limits(m->L, r.dim);
   if (e != cudaSuccess) {
@@ -342,6 +361,8 @@ esd_status esd_mesh_check(esd_mesh m, void* stream) {
     cudaMemset(m->M.flag, 0, sizeof(int));
     if (flag & kFlagTimeout)
       return fail(ESD_ERR_TIMEOUT, "a shared-memory staging copy did not complete within its time limit");
+    if (flag & kFlagIndex)
+      return fail(ESD_ERR_ARG, "esd_part_export: an element index is outside [0, n_elem) (zeros were sent)");
     return fail(ESD_ERR_STATE, "non-admissible state (rho <= 0, p <= 0 or non-finite) at a quadrature node");
   }
   return ESD_OK;
@@ -391,6 +412,7 @@ esd_status esd_rhs(esd_mesh m, const double* u, double* dudt, void* stream) {
   ESD_RANGE("esd_rhs");
   if (!m) return fail(ESD_ERR_ARG, "null mesh");
   if (esd_status ds = check_device(m->device)) return ds;
+  if (esd_status ps = reject_partition(m, "esd_rhs")) return ps;
   esd_status st;
   if ((st = check_dev(u, "u")) || (st = check_dev(dudt, "dudt"))) return st;
   if (u == dudt) return fail(ESD_ERR_ARG, "u and dudt must not alias");
@@ -404,7 +426,56 @@ esd_status esd_rhs(esd_mesh m, const double* u, double* dudt, void* stream) {
   return e ? cuda_fail(e, "residual launch") : ESD_OK;
 }
 
-static cudaError_t rk_sequence(esd_mesh m, double* u, double dt, double* ck, cudaStream_t s) {
+// Forward tape (esd_rhs_save, esd_rk_step_save): the entropy-projected states with their
+// derived fields, [E][nfields][Ntot], padded to a multiple of 32 doubles (256 bytes), then
+// the facet sound speeds [E][Nfn], padded the same way: what the projection kernel writes and the residual kernel
+// and the VJP kernels read.
+static size_t tape_states_doubles(const esd_mesh_s* m) {
+  return ((size_t)m->E * nfields(m->dim) * m->ref.Ntot + 31) / 32 * 32;
+}
+static size_t tape_doubles(const esd_mesh_s* m) {   // a multiple of 32: stage tapes stay aligned
+  return tape_states_doubles(m) + ((size_t)m->E * m->ref.Nfn + 31) / 32 * 32;
+}
+static DevMesh on_tape(const esd_mesh_s* m, const double* tape) {
+  DevMesh M = m->M;
+  M.states = const_cast<double*>(tape);   // read-only for the VJP kernels
+  M.cfac = const_cast<double*>(tape) + tape_states_doubles(m);
+  return M;
+}
+// the residual kernel stages each element's states with a bulk copy: 16-byte alignment
+static esd_status check_tape(const void* t, const char* name) {
+  if (esd_status st = check_dev(t, name)) return st;
+  if (reinterpret_cast<uintptr_t>(t) % 16 != 0) return fail(ESD_ERR_ARG, std::string(name) + " is not 16-byte aligned");
+  return ESD_OK;
+}
+
+esd_status esd_tape_doubles(esd_mesh m, int64_t* n_doubles) {
+  if (!m || !n_doubles) return fail(ESD_ERR_ARG, "null argument");
+  *n_doubles = (int64_t)tape_doubles(m);
+  return ESD_OK;
+}
+
+esd_status esd_rhs_save(esd_mesh m, const double* u, double* dudt, double* tape, void* stream) {
+  ESD_RANGE("esd_rhs_save");
+  if (!m) return fail(ESD_ERR_ARG, "null mesh");
+  if (esd_status ds = check_device(m->device)) return ds;
+  if (esd_status ps = reject_partition(m, "esd_rhs_save")) return ps;
+  if (m->M.gvol) return fail(ESD_ERR_UNSUPPORTED, "the VJP needs the stored pair tables (esd_mesh_create)");
+  esd_status st;
+  if ((st = check_dev(u, "u")) || (st = check_dev(dudt, "dudt")) || (st = check_tape(tape, "tape"))) return st;
+  if (u == dudt) return fail(ESD_ERR_ARG, "u and dudt must not alias");
+  cudaStream_t s = (cudaStream_t)stream;
+  const DevMesh M = on_tape(m, tape);
+  cudaError_t e = launch_project(m->R, M, m->L, u, nullptr, s);
+  if (e) return cuda_fail(e, "project launch");
+  Epilogue ep{};
+  ep.mode = 0;
+  ep.dudt = dudt;
+  e = launch_residual(m->R, M, m->L, ep, s);
+  return e ? cuda_fail(e, "residual launch") : ESD_OK;
+}
+
+static cudaError_t rk_sequence(esd_mesh m, double* u, double dt, double* ck, double* tapes, cudaStream_t s) {
   const size_t nmodal = (size_t)m->E * m->nc * m->ref.Np;
   cudaError_t e;
   if (ck && (e = launch_copy(u, ck, (int64_t)nmodal, s))) return e;
@@ -412,7 +483,8 @@ static cudaError_t rk_sequence(esd_mesh m, double* u, double dt, double* ck, cud
   const double b[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
   const double* in = u;
   for (int st = 0; st < 4; ++st) {
-    if ((e = launch_project(m->R, m->M, m->L, in, nullptr, s))) return e;
+    const DevMesh M = tapes ? on_tape(m, tapes + st * tape_doubles(m)) : m->M;
+    if ((e = launch_project(m->R, M, m->L, in, nullptr, s))) return e;
     Epilogue ep{};
     ep.mode = 1;
     ep.u0 = u;
@@ -421,34 +493,35 @@ static cudaError_t rk_sequence(esd_mesh m, double* u, double dt, double* ck, cud
     ep.stage_out = st == 3 ? nullptr : (ck ? ck + (size_t)(st + 1) * nmodal : m->ws_stage);
     ep.ca = a[st] * dt;
     ep.cb = b[st] * dt;
-    if ((e = launch_residual(m->R, m->M, m->L, ep, s))) return e;
+    if ((e = launch_residual(m->R, M, m->L, ep, s))) return e;
     in = ep.stage_out;
   }
   return cudaSuccess;
 }
 
-esd_status esd_rk_step(esd_mesh m, double* u, double dt, double* ck, void* stream) {
-  ESD_RANGE("esd_rk_step");
+static esd_status rk_step(esd_mesh m, double* u, double dt, double* ck, double* tapes, void* stream) {
   if (!m) return fail(ESD_ERR_ARG, "null mesh");
   if (esd_status ds = check_device(m->device)) return ds;
+  if (esd_status ps = reject_partition(m, "esd_rk_step")) return ps;
   esd_status st;
   if ((st = check_dev(u, "u"))) return st;
   if (ck && (st = check_dev(ck, "stage_ckpt"))) return st;
+  if (tapes && (st = check_tape(tapes, "tapes"))) return st;
   if (!(dt == dt) || dt <= 0.0) return fail(ESD_ERR_ARG, "dt must be positive");
   cudaStream_t s = (cudaStream_t)stream;
   if (s == nullptr) {  // the legacy stream cannot be captured: launch directly
-    cudaError_t e = rk_sequence(m, u, dt, ck, s);
+    cudaError_t e = rk_sequence(m, u, dt, ck, tapes, s);
     return e ? cuda_fail(e, "rk launch") : ESD_OK;
   }
   for (auto& g : m->graphs)
-    if (g.u == u && g.dt == dt && g.ckpt == ck && g.s == s) {
+    if (g.u == u && g.dt == dt && g.ckpt == ck && g.tapes == tapes && g.s == s) {
       cudaError_t e = cudaGraphLaunch(g.exec, s);
       return e ? cuda_fail(e, "graph launch") : ESD_OK;
     }
   cudaGraph_t graph;
   cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
   if (e) return cuda_fail(e, "begin capture");
-  cudaError_t e1 = rk_sequence(m, u, dt, ck, s);
+  cudaError_t e1 = rk_sequence(m, u, dt, ck, tapes, s);
   e = cudaStreamEndCapture(s, &graph);
   if (e1 || e) {
     if (!e) cudaGraphDestroy(graph);
@@ -462,15 +535,29 @@ esd_status esd_rk_step(esd_mesh m, double* u, double dt, double* ck, void* strea
     cudaGraphExecDestroy(m->graphs.front().exec);   // an in-flight launch completes first
     m->graphs.erase(m->graphs.begin());
   }
-  m->graphs.push_back({u, dt, ck, s, exec});
+  m->graphs.push_back({u, dt, ck, tapes, s, exec});
   e = cudaGraphLaunch(exec, s);
   return e ? cuda_fail(e, "graph launch") : ESD_OK;
+}
+
+esd_status esd_rk_step(esd_mesh m, double* u, double dt, double* ck, void* stream) {
+  ESD_RANGE("esd_rk_step");
+  return rk_step(m, u, dt, ck, nullptr, stream);
+}
+
+esd_status esd_rk_step_save(esd_mesh m, double* u, double dt, double* ck, double* tapes, void* stream) {
+  ESD_RANGE("esd_rk_step_save");
+  if (!m) return fail(ESD_ERR_ARG, "null mesh");
+  if (!ck || !tapes) return fail(ESD_ERR_ARG, "esd_rk_step_save needs stage_ckpt and tapes");
+  if (m->M.gvol) return fail(ESD_ERR_UNSUPPORTED, "the VJP needs the stored pair tables (esd_mesh_create)");
+  return rk_step(m, u, dt, ck, tapes, stream);
 }
 
 esd_status esd_diagnostics(esd_mesh m, const double* u, double* out, void* stream) {
   ESD_RANGE("esd_diagnostics");
   if (!m) return fail(ESD_ERR_ARG, "null mesh");
   if (esd_status ds = check_device(m->device)) return ds;
+  if (esd_status ps = reject_partition(m, "esd_diagnostics")) return ps;
   esd_status st;
   if ((st = check_dev(u, "u")) || (st = check_dev(out, "out"))) return st;
   cudaStream_t s = (cudaStream_t)stream;
@@ -497,15 +584,19 @@ esd_status esd_integrals(esd_mesh m, const double* u, double* out, void* stream)
   return e ? cuda_fail(e, "reduce launch") : ESD_OK;
 }
 
-esd_status esd_rhs_vjp(esd_mesh m, const double* u, const double* cot, double* grad, void* stream) {
-  ESD_RANGE("esd_rhs_vjp");
+// tape: null (the projection of u is recomputed first) or the forward's saved tape of u
+static esd_status rhs_vjp(esd_mesh m, const double* u, const double* tape, const double* cot, double* grad,
+                          void* stream) {
   if (!m) return fail(ESD_ERR_ARG, "null mesh");
   if (esd_status ds = check_device(m->device)) return ds;
+  if (esd_status ps = reject_partition(m, "esd_rhs_vjp")) return ps;
   if (m->M.gvol) return fail(ESD_ERR_UNSUPPORTED, "the VJP needs the stored pair tables (esd_mesh_create)");
   esd_status st;
   if ((st = check_dev(u, "u")) || (st = check_dev(cot, "cot")) || (st = check_dev(grad, "grad"))) return st;
   if (grad == u || grad == cot) return fail(ESD_ERR_ARG, "grad must not alias u or cot");
-  cudaError_t e = launch_vjp(m->R, m->M, m->L, u, cot, grad, m->ws_qbar, m->ws_qext, (cudaStream_t)stream);
+  if (tape && (st = check_tape(tape, "tape"))) return st;
+  const DevMesh M = tape ? on_tape(m, tape) : m->M;
+  cudaError_t e = launch_vjp(m->R, M, m->L, u, cot, grad, m->ws_qbar, m->ws_qext, (cudaStream_t)stream, !tape);
   return e ? cuda_fail(e, "vjp launch") : ESD_OK;
 }
 
@@ -514,14 +605,17 @@ esd_status esd_rhs_vjp(esd_mesh m, const double* u, const double* cot, double* g
 // Reverse: k4_b = dt/6 c;  Y4_b = J(Y4)^T k4_b;  k3_b = dt/3 c + dt Y4_b;  Y3_b = J(Y3)^T k3_b;
 //          k2_b = dt/3 c + dt/2 Y3_b;  Y2_b = J(Y2)^T k2_b;  k1_b = dt/6 c + dt/2 Y2_b;
 //          Y1_b = J(Y1)^T k1_b;  u_b = c + Y1_b + Y2_b + Y3_b + Y4_b.
-esd_status esd_rk_step_vjp(esd_mesh m, const double* ck, double dt, const double* co, double* ci, void* stream) {
-  ESD_RANGE("esd_rk_step_vjp");
+// tapes: null (each stage's projection is recomputed) or the four stages' saved tapes
+static esd_status rk_step_vjp(esd_mesh m, const double* ck, const double* tapes, double dt, const double* co,
+                              double* ci, void* stream) {
   if (!m) return fail(ESD_ERR_ARG, "null mesh");
   if (esd_status ds = check_device(m->device)) return ds;
+  if (esd_status ps = reject_partition(m, "esd_rk_step_vjp")) return ps;
   if (m->M.gvol) return fail(ESD_ERR_UNSUPPORTED, "the VJP needs the stored pair tables (esd_mesh_create)");
   esd_status st;
   if ((st = check_dev(ck, "stage_ckpt")) || (st = check_dev(co, "cot_out")) || (st = check_dev(ci, "cot_in")))
     return st;
+  if (tapes && (st = check_tape(tapes, "tapes"))) return st;
   if (!(dt == dt) || dt <= 0.0) return fail(ESD_ERR_ARG, "dt must be positive");
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t nmodal = m->E * m->nc * m->ref.Np;
@@ -533,11 +627,125 @@ esd_status esd_rk_step_vjp(esd_mesh m, const double* ck, double dt, const double
   for (int j = 0; j < 4; ++j) {
     const int stage = 3 - j;  // Y4, Y3, Y2, Y1
     if ((e = launch_axpby(kb, ck_a[j], c, ck_b[j], j ? yb : nullptr, nmodal, s))) return cuda_fail(e, "rk vjp");
-    if ((e = launch_vjp(m->R, m->M, m->L, ck + (size_t)stage * nmodal, kb, yb, m->ws_qbar, m->ws_qext, s)))
+    const DevMesh M = tapes ? on_tape(m, tapes + stage * tape_doubles(m)) : m->M;
+    if ((e = launch_vjp(m->R, M, m->L, ck + (size_t)stage * nmodal, kb, yb, m->ws_qbar, m->ws_qext, s, !tapes)))
       return cuda_fail(e, "rk vjp");
     if ((e = launch_axpby(j == 3 ? ci : acc, 1.0, acc, 1.0, yb, nmodal, s))) return cuda_fail(e, "rk vjp");
   }
   return ESD_OK;
+}
+
+esd_status esd_rhs_vjp(esd_mesh m, const double* u, const double* cot, double* grad, void* stream) {
+  ESD_RANGE("esd_rhs_vjp");
+  return rhs_vjp(m, u, nullptr, cot, grad, stream);
+}
+
+esd_status esd_rhs_vjp_saved(esd_mesh m, const double* u, const double* tape, const double* cot, double* grad,
+                             void* stream) {
+  ESD_RANGE("esd_rhs_vjp_saved");
+  if (!tape) return fail(ESD_ERR_ARG, "null tape");
+  return rhs_vjp(m, u, tape, cot, grad, stream);
+}
+
+esd_status esd_rk_step_vjp(esd_mesh m, const double* ck, double dt, const double* co, double* ci, void* stream) {
+  ESD_RANGE("esd_rk_step_vjp");
+  return rk_step_vjp(m, ck, nullptr, dt, co, ci, stream);
+}
+
+esd_status esd_rk_step_vjp_saved(esd_mesh m, const double* ck, const double* tapes, double dt, const double* co,
+                                 double* ci, void* stream) {
+  ESD_RANGE("esd_rk_step_vjp_saved");
+  if (!tapes) return fail(ESD_ERR_ARG, "null tapes");
+  return rk_step_vjp(m, ck, tapes, dt, co, ci, stream);
+}
+
+// ---------------------------------------------------------------------------
+// Element partitions: one facet-trace exchange per right-hand side (and one cotangent
+// exchange per VJP) between the phases of the evaluation.
+// ---------------------------------------------------------------------------
+esd_status esd_part_create(const esd_mesh_desc* d, int64_t n_ghost, esd_mesh* out) {
+  if (!d || !out) return fail(ESD_ERR_ARG, "null descriptor or output");
+  if (n_ghost < 0 || n_ghost >= d->n_elem) return fail(ESD_ERR_ARG, "n_ghost must be in [0, n_elem)");
+  return mesh_create(d, kTablesEntropyStable, out, n_ghost);
+}
+
+esd_status esd_part_info(esd_mesh m, int64_t* n_ghost, int64_t* trace_doubles, int64_t* cotangent_doubles) {
+  if (!m) return fail(ESD_ERR_ARG, "null mesh");
+  const int64_t Nfn = m->ref.Nfn;
+  if (n_ghost) *n_ghost = m->n_ghost;
+  if (trace_doubles) *trace_doubles = (nfields(m->dim) + 1) * Nfn;
+  if (cotangent_doubles) *cotangent_doubles = m->nc * Nfn;
+  return ESD_OK;
+}
+
+esd_status esd_rhs_begin(esd_mesh m, const double* u, void* stream) {
+  ESD_RANGE("esd_rhs_begin");
+  if (!m) return fail(ESD_ERR_ARG, "null mesh");
+  if (esd_status ds = check_device(m->device)) return ds;
+  if (esd_status st = check_dev(u, "u")) return st;
+  cudaError_t e = launch_project(m->R, m->M, m->L, u, nullptr, (cudaStream_t)stream);
+  return e ? cuda_fail(e, "project launch") : ESD_OK;
+}
+
+esd_status esd_rhs_end(esd_mesh m, double* dudt, void* stream) {
+  ESD_RANGE("esd_rhs_end");
+  if (!m) return fail(ESD_ERR_ARG, "null mesh");
+  if (esd_status ds = check_device(m->device)) return ds;
+  if (esd_status st = check_dev(dudt, "dudt")) return st;
+  Epilogue ep{};
+  ep.mode = 0;
+  ep.dudt = dudt;
+  cudaError_t e = launch_residual(m->R, m->M, m->L, ep, (cudaStream_t)stream);
+  return e ? cuda_fail(e, "residual launch") : ESD_OK;
+}
+
+esd_status esd_rhs_vjp_mid(esd_mesh m, const double* cot, void* stream) {
+  ESD_RANGE("esd_rhs_vjp_mid");
+  if (!m) return fail(ESD_ERR_ARG, "null mesh");
+  if (esd_status ds = check_device(m->device)) return ds;
+  if (m->M.gvol || !m->ws_qbar) return fail(ESD_ERR_UNSUPPORTED, "the VJP needs the stored pair tables (esd_mesh_create)");
+  if (esd_status st = check_dev(cot, "cot")) return st;
+  cudaError_t e = launch_residual_adjoint(m->R, m->M, m->L, cot, m->ws_qbar, m->ws_qext, (cudaStream_t)stream);
+  return e ? cuda_fail(e, "residual adjoint launch") : ESD_OK;
+}
+
+esd_status esd_rhs_vjp_end(esd_mesh m, const double* u, double* grad, void* stream) {
+  ESD_RANGE("esd_rhs_vjp_end");
+  if (!m) return fail(ESD_ERR_ARG, "null mesh");
+  if (esd_status ds = check_device(m->device)) return ds;
+  if (m->M.gvol || !m->ws_qbar) return fail(ESD_ERR_UNSUPPORTED, "the VJP needs the stored pair tables (esd_mesh_create)");
+  esd_status st;
+  if ((st = check_dev(u, "u")) || (st = check_dev(grad, "grad"))) return st;
+  if (grad == u) return fail(ESD_ERR_ARG, "grad must not alias u");
+  cudaError_t e = launch_project_adjoint(m->R, m->M, m->L, u, m->ws_qbar, m->ws_qext, grad, (cudaStream_t)stream);
+  return e ? cuda_fail(e, "projection adjoint launch") : ESD_OK;
+}
+
+esd_status esd_part_export(esd_mesh m, int kind, const int64_t* elems, int64_t n, double* buf, void* stream) {
+  ESD_RANGE("esd_part_export");
+  if (!m) return fail(ESD_ERR_ARG, "null mesh");
+  if (esd_status ds = check_device(m->device)) return ds;
+  if (kind != ESD_TRACE_STATES && kind != ESD_TRACE_COTANGENTS) return fail(ESD_ERR_ARG, "unknown trace kind");
+  if (kind == ESD_TRACE_COTANGENTS && !m->ws_qext) return fail(ESD_ERR_UNSUPPORTED, "this mesh has no VJP");
+  if (n < 0) return fail(ESD_ERR_ARG, "n must be >= 0");
+  if (n == 0) return ESD_OK;
+  esd_status st;
+  if ((st = check_dev(elems, "elems")) || (st = check_dev(buf, "buf"))) return st;
+  cudaError_t e = launch_trace_export(m->R, m->M, m->ws_qext, kind, elems, n, buf, (cudaStream_t)stream);
+  return e ? cuda_fail(e, "trace export launch") : ESD_OK;
+}
+
+esd_status esd_part_import(esd_mesh m, int kind, const double* buf, int64_t first, int64_t n, void* stream) {
+  ESD_RANGE("esd_part_import");
+  if (!m) return fail(ESD_ERR_ARG, "null mesh");
+  if (esd_status ds = check_device(m->device)) return ds;
+  if (kind != ESD_TRACE_STATES && kind != ESD_TRACE_COTANGENTS) return fail(ESD_ERR_ARG, "unknown trace kind");
+  if (kind == ESD_TRACE_COTANGENTS && !m->ws_qext) return fail(ESD_ERR_UNSUPPORTED, "this mesh has no VJP");
+  if (first < 0 || n < 0 || first + n > m->n_ghost) return fail(ESD_ERR_ARG, "ghost range outside [0, n_ghost)");
+  if (n == 0) return ESD_OK;
+  if (esd_status st = check_dev(buf, "buf")) return st;
+  cudaError_t e = launch_trace_import(m->R, m->M, m->ws_qext, kind, buf, first, n, (cudaStream_t)stream);
+  return e ? cuda_fail(e, "trace import launch") : ESD_OK;
 }
 
 struct BatchGroup {
@@ -593,6 +801,8 @@ esd_status esd_batch_create(const esd_mesh* meshes, int n, esd_batch* out) {
     if (esd_status ds = check_device(meshes[i]->device)) return ds;
   for (int i = 0; i < n; ++i)
     if (meshes[i]->M.gvol) return fail(ESD_ERR_UNSUPPORTED, "batches need meshes with stored pair tables");
+  for (int i = 0; i < n; ++i)
+    if (esd_status ps = reject_partition(meshes[i], "esd_batch_create")) return ps;
   esd_batch b = new esd_batch_s();
   b->meshes.assign(meshes, meshes + n);
   const int sms = sm_count();
@@ -852,6 +1062,7 @@ esd_status static_scratch_address(double** out) {
 esd_status esd_rhs_static_scratch(esd_mesh m, const double* u, double* dudt, void* stream) {
   if (!m) return fail(ESD_ERR_ARG, "null mesh");
   if (esd_status ds = check_device(m->device)) return ds;
+  if (esd_status ps = reject_partition(m, "esd_rhs_static_scratch")) return ps;
   esd_status st;
   if ((st = check_dev(u, "u")) || (st = check_dev(dudt, "dudt"))) return st;
   if (u == dudt) return fail(ESD_ERR_ARG, "u and dudt must not alias");

@@ -71,8 +71,10 @@ constexpr int kTablesSkew = 2;            // sdir (the skew-symmetric form, skew
 constexpr int kTablesMetrics = 4;         // gvol, jnf (pair directions formed on the fly)
 
 esd_status build_ref(int dim, int p, RefTables* out, std::string* err);
+// n_ghost > 0: a partition mesh whose last n_ghost elements are ghosts (esd_part_create):
+// geometry for all, facet matching and the returned tables for the local elements only
 esd_status build_host_mesh(const esd_mesh_desc& d, HostMesh* out, std::string* err,
-                           int tables = kTablesEntropyStable);
+                           int tables = kTablesEntropyStable, int64_t n_ghost = 0);
 
 // Device views passed to kernels by value.
 // Tables of the table-driven logarithm and exponential (device.cuh: log_tab, exp_tab),
@@ -102,6 +104,7 @@ struct DevRef {
 // bits of DevMesh::flag (read and cleared by esd_mesh_check)
 constexpr int kFlagState = 1;     // a non-admissible state (rho <= 0, p <= 0, non-finite)
 constexpr int kFlagTimeout = 2;   // a shared-memory staging copy did not complete in time
+constexpr int kFlagIndex = 4;     // a trace export named an element outside the partition
 
 struct DevMesh {
   int64_t E;
@@ -163,8 +166,19 @@ cudaError_t launch_residual(const DevRef& R, const DevMesh& M, const LaunchCfg& 
                             cudaStream_t s);
 cudaError_t launch_l2_project(const DevRef& R, const DevMesh& M, const double* un, double* um,
                               cudaStream_t s);
+// project_first = false: M.states / M.cfac already hold the entropy projection of u
+// (a tape saved by the forward call), so the projection kernel is not launched again
 cudaError_t launch_vjp(const DevRef& R, const DevMesh& M, const LaunchCfg& L, const double* u, const double* cot,
-                       double* grad, double* qbar, double* qext, cudaStream_t s);
+                       double* grad, double* qbar, double* qext, cudaStream_t s, bool project_first = true);
+cudaError_t launch_residual_adjoint(const DevRef& R, const DevMesh& M, const LaunchCfg& L, const double* cot,
+                                    double* qbar, double* qext, cudaStream_t s);
+cudaError_t launch_project_adjoint(const DevRef& R, const DevMesh& M, const LaunchCfg& L, const double* u,
+                                   const double* qbar, const double* qext, double* grad, cudaStream_t s);
+// partition trace messages (kind 0: states and sound speeds; kind 1: interface cotangents)
+cudaError_t launch_trace_export(const DevRef& R, const DevMesh& M, const double* qext, int kind,
+                                const int64_t* elems, int64_t n, double* buf, cudaStream_t s);
+cudaError_t launch_trace_import(const DevRef& R, const DevMesh& M, double* qext, int kind, const double* buf,
+                                int64_t first, int64_t n, cudaStream_t s);
 cudaError_t launch_axpby(double* out, double a, const double* x, double b, const double* y, int64_t n,
                          cudaStream_t s);
 cudaError_t launch_batch(int dim, int n, int stage, const BatchMesh* meshes, const BatchItem* items, int nitems,

@@ -729,21 +729,94 @@ size_t smem_residual_adj(const RefTables& r, int e) {
   return (size_t)e * L.pe * sizeof(double);
 }
 
-cudaError_t launch_vjp(const DevRef& R, const DevMesh& M, const LaunchCfg& L, const double* u, const double* cot,
-                       double* grad, double* qbar, double* qext, cudaStream_t s) {
-  cudaError_t e = launch_project(R, M, L, u, nullptr, s);
-  if (e) return e;
+cudaError_t launch_residual_adjoint(const DevRef& R, const DevMesh& M, const LaunchCfg& L, const double* cot,
+                                    double* qbar, double* qext, cudaStream_t s) {
   const unsigned gb = (unsigned)((M.E + L.ev - 1) / L.ev);
   if (R.dim == 2)
     residual_adjoint_kernel<2><<<gb, L.tv, L.sv, s>>>(R, M, L.ev, cot, qbar, qext);
   else
     residual_adjoint_kernel<3><<<gb, L.tv, L.sv, s>>>(R, M, L.ev, cot, qbar, qext);
-  if ((e = cudaGetLastError())) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_project_adjoint(const DevRef& R, const DevMesh& M, const LaunchCfg& L, const double* u,
+                                   const double* qbar, const double* qext, double* grad, cudaStream_t s) {
   const unsigned ga = (unsigned)((M.E + L.eq - 1) / L.eq);
   if (R.dim == 2)
     project_adjoint_kernel<2><<<ga, L.tq, L.sq, s>>>(R, M, L.eq, u, qbar, qext, grad);
   else
     project_adjoint_kernel<3><<<ga, L.tq, L.sq, s>>>(R, M, L.eq, u, qbar, qext, grad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_vjp(const DevRef& R, const DevMesh& M, const LaunchCfg& L, const double* u, const double* cot,
+                       double* grad, double* qbar, double* qext, cudaStream_t s, bool project_first) {
+  cudaError_t e;
+  if (project_first && (e = launch_project(R, M, L, u, nullptr, s))) return e;
+  if ((e = launch_residual_adjoint(R, M, L, cot, qbar, qext, s))) return e;
+  return launch_project_adjoint(R, M, L, u, qbar, qext, grad, s);
+}
+
+// Trace messages of a partition mesh (esd_part_export / esd_part_import), per element:
+// kind 0 (forward), the facet-node columns of the states [nfields][Nfn] then the facet sound
+// speeds [Nfn]; kind 1 (VJP), the interface cotangents [nc][Nfn] of the residual adjoint.
+// Export reads local elements elems[0..n); an index outside [0, E) sets kFlagIndex and sends
+// zeros.  Import writes ghost rows E + first .. E + first + n - 1 (range checked on the host).
+__global__ void trace_export_kernel(DevRef R, DevMesh M, const double* __restrict__ qext, int kind,
+                                    const int64_t* __restrict__ elems, int64_t n, double* __restrict__ buf) {
+  const int nf = R.dim + 5, nc = R.dim + 2, Nfn = R.Nfn, Nq = R.Nq, Ntot = R.Ntot;
+  const int per = kind == 0 ? (nf + 1) * Nfn : nc * Nfn;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n * per; idx += stride) {
+    const int64_t i = idx / per;
+    const int r = (int)(idx - i * per);
+    const int64_t e = elems[i];
+    double v = 0.0;
+    if (e < 0 || e >= M.E) {
+      if (r == 0) atomicOr(M.flag, kFlagIndex);
+    } else if (kind == 0) {
+      const int c = r / Nfn, k = r - c * Nfn;
+      v = c < nf ? M.states[(e * nf + c) * Ntot + Nq + k] : M.cfac[e * Nfn + k];
+    } else {
+      v = qext[e * (int64_t)(nc * Nfn) + r];
+    }
+    buf[idx] = v;
+  }
+}
+
+__global__ void trace_import_kernel(DevRef R, DevMesh M, double* __restrict__ qext, int kind,
+                                    const double* __restrict__ buf, int64_t first, int64_t n) {
+  const int nf = R.dim + 5, nc = R.dim + 2, Nfn = R.Nfn, Nq = R.Nq, Ntot = R.Ntot;
+  const int per = kind == 0 ? (nf + 1) * Nfn : nc * Nfn;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n * per; idx += stride) {
+    const int64_t i = idx / per;
+    const int r = (int)(idx - i * per);
+    const int64_t e = M.E + first + i;   // ghost row
+    const double v = buf[idx];
+    if (kind == 0) {
+      const int c = r / Nfn, k = r - c * Nfn;
+      if (c < nf)
+        M.states[(e * nf + c) * Ntot + Nq + k] = v;
+      else
+        M.cfac[e * Nfn + k] = v;
+    } else {
+      qext[e * (int64_t)(nc * Nfn) + r] = v;
+    }
+  }
+}
+
+cudaError_t launch_trace_export(const DevRef& R, const DevMesh& M, const double* qext, int kind,
+                                const int64_t* elems, int64_t n, double* buf, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  trace_export_kernel<<<152 * 4, 256, 0, s>>>(R, M, qext, kind, elems, n, buf);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_trace_import(const DevRef& R, const DevMesh& M, double* qext, int kind, const double* buf,
+                                int64_t first, int64_t n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  trace_import_kernel<<<152 * 4, 256, 0, s>>>(R, M, qext, kind, buf, first, n);
   return cudaGetLastError();
 }
 

@@ -465,7 +465,7 @@ double det(int d, const double* A) {  // A[m*d+k] = d x_m / d xi_k
 
 }  // namespace
 
-esd_status build_host_mesh(const esd_mesh_desc& d, HostMesh* H, std::string* err, int tables) {
+esd_status build_host_mesh(const esd_mesh_desc& d, HostMesh* H, std::string* err, int tables, int64_t n_ghost) {
   const bool es = (tables & kTablesEntropyStable) != 0, skew = (tables & kTablesSkew) != 0;
   const bool metrics = (tables & kTablesMetrics) != 0;
   esd_status st = build_ref(d.dim, d.p, &H->ref, err);
@@ -473,7 +473,14 @@ esd_status build_host_mesh(const esd_mesh_desc& d, HostMesh* H, std::string* err
   const RefTables& r = H->ref;
   const int dim = r.dim, n = r.n, Nq = r.Nq, Nfn = r.Nfn, Nqf = r.Nqf, T = r.T;
   const int64_t E = d.n_elem;
-  H->E = E;
+  // partition meshes: the last n_ghost elements are ghosts; their geometry is computed (their
+  // facet nodes are matched against the local elements') but only local elements are kept
+  if (n_ghost < 0 || n_ghost >= E) {
+    *err = "n_ghost must be in [0, n_elem)";
+    return ESD_ERR_ARG;
+  }
+  const int64_t El = E - n_ghost;
+  H->E = El;
   Lattice Lmap = make_lattice(dim, d.p);
   const int nmap = Lmap.size();
   // points: volume nodes, facet nodes, mapping lattice nodes, (3D) curl interpolation nodes
@@ -764,8 +771,8 @@ esd_status build_host_mesh(const esd_mesh_desc& d, HostMesh* H, std::string* err
     int a = j % n, b = j / n;
     perm_rev[j] = dim == 2 ? n - 1 - j : (n - 1 - a) + n * b;
   }
-  std::vector<int> fail(E, 0);
-  auto match = [&](int64_t e0, int64_t e1) {
+  std::vector<int> fail(El, 0);
+  auto match = [&](int64_t e0, int64_t e1) {   // local elements only: ghosts are not computed
     for (int64_t e = e0; e < e1; ++e)
       for (int z = 0; z < r.Nf; ++z) {
         int64_t e2 = d.nbr_elem[e * r.Nf + z];
@@ -813,14 +820,14 @@ esd_status build_host_mesh(const esd_mesh_desc& d, HostMesh* H, std::string* err
   {
     unsigned nth = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
     std::vector<std::thread> th;
-    int64_t chunk = (E + nth - 1) / nth;
+    int64_t chunk = (El + nth - 1) / nth;
     for (unsigned i = 0; i < nth; ++i) {
-      int64_t a = i * chunk, b = std::min<int64_t>(E, a + chunk);
+      int64_t a = i * chunk, b = std::min<int64_t>(El, a + chunk);
       if (a < b) th.emplace_back(match, a, b);
     }
     for (auto& t : th) t.join();
   }
-  for (int64_t e = 0; e < E; ++e)
+  for (int64_t e = 0; e < El; ++e)
     if (fail[e]) {
       static const char* why[] = {"", "neighbour index out of range", "connectivity not symmetric",
                                   "facet nodes do not coincide with the neighbour's",
@@ -830,6 +837,11 @@ esd_status build_host_mesh(const esd_mesh_desc& d, HostMesh* H, std::string* err
       *err = o.str();
       return ESD_ERR_MESH;
     }
+  if (n_ghost > 0) {   // keep the local elements' tables ([E][...] arrays, element-major)
+    auto keep = [&](auto& v) { v.resize(v.size() / (size_t)E * (size_t)El); };
+    keep(H->vdir); keep(H->fdir); keep(H->sdir); keep(H->gvol); keep(H->jnf); keep(H->wj); keep(H->wdj);
+    keep(H->bj); keep(H->nrm); keep(H->nbr_e); keep(H->nbr_f); keep(H->xvol); keep(H->minv);
+  }
   return ESD_OK;
 }
 

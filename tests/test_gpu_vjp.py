@@ -159,3 +159,90 @@ def test_vjp_torch_function():
     jv = jvp(D, um, v)
     assert abs(float((u.grad.cpu() * torch.from_numpy(v)).sum()) - np.sum(c.cpu().numpy() * jv)) < \
         1e-11 * np.sum(np.abs(c.cpu().numpy() * jv))
+
+
+# Reverse mode with saved forward tapes: the _saved calls read the entropy-projected states
+# the forward left in the tape instead of recomputing them, with the same kernels on the same
+# values, so everything must agree bit for bit with the recomputing calls.
+@pytest.mark.parametrize("dim,M,p,state,flux", [(2, 4, 4, "vortex", "LF"), (3, 3, 3, "tgv", "EC"),
+                                               (3, 3, 4, "density_wave", "LF")])
+def test_saved_tape_vjp_bitwise(dim, M, p, state, flux):
+    import torch
+    import paper_2312_07874_gb300 as E
+    mesh, X, D, um = workload(dim, M, p, True, flux, state)
+    gm = gpu_mesh(dim, p, X, mesh, flux)
+    rng = np.random.default_rng(13)
+    u, c = to_dev(um), to_dev(rng.standard_normal(um.shape))
+    tape = gm.empty_tapes()
+    r0, r1 = torch.empty_like(u), torch.empty_like(u)
+    E.esd_rhs(gm.handle, u, r0)
+    E.esd_rhs_save(gm.handle, u, r1, tape)
+    assert torch.equal(r0, r1)
+    # the mesh workspace is overwritten by another state: the saved VJP must not read it
+    E.esd_rhs(gm.handle, 1.02 * u, r0)
+    g0, g1 = torch.empty_like(u), torch.empty_like(u)
+    E.esd_rhs_vjp(gm.handle, u, c, g0)
+    E.esd_rhs(gm.handle, 1.01 * u, r0)
+    E.esd_rhs_vjp_saved(gm.handle, u, tape, c, g1)
+    gm.check()
+    assert torch.equal(g0, g1)
+    # one RK4 step with its four stage tapes, and its adjoint
+    dt = 2e-3
+    ua, ub = u.clone(), u.clone()
+    cka = torch.empty((4,) + u.shape, dtype=torch.float64, device="cuda")
+    ckb = torch.empty_like(cka)
+    tapes = gm.empty_tapes(4)
+    E.esd_rk_step(gm.handle, ua, dt, cka)
+    E.esd_rk_step_save(gm.handle, ub, dt, ckb, tapes)
+    assert torch.equal(ua, ub) and torch.equal(cka, ckb)
+    E.esd_rhs(gm.handle, 0.99 * u, r0)
+    ca, cb = torch.empty_like(u), torch.empty_like(u)
+    E.esd_rk_step_vjp(gm.handle, cka, dt, c, ca)
+    E.esd_rk_step_vjp_saved(gm.handle, ckb, tapes, dt, c, cb)
+    gm.check()
+    assert torch.equal(ca, cb)
+
+
+def test_saved_tape_rollout_and_rhs_function():
+    """The "tapes" rollout gives the "stages" rollout's gradient bit for bit; so does the
+    autograd Rhs with and without its tape."""
+    import torch
+    from paper_2312_07874_gb300.autograd import Rhs, rollout
+    mesh, X, D, um = workload(3, 3, 3, True, "EC", "tgv")
+    gm = gpu_mesh(3, 3, X, mesh, "EC")
+    rng = np.random.default_rng(14)
+    w = to_dev(rng.standard_normal(um.shape))
+    grads = []
+    for mode in ("stages", "tapes"):
+        u0 = to_dev(um).requires_grad_(True)
+        (w * rollout(u0, gm, 2e-3, 5, mode)).sum().backward()
+        grads.append(u0.grad)
+    assert torch.equal(grads[0], grads[1])
+    grads = []
+    for save in (False, True):
+        u0 = to_dev(um).requires_grad_(True)
+        (w * Rhs.apply(u0, gm, save)).sum().backward()
+        grads.append(u0.grad)
+    assert torch.equal(grads[0], grads[1])
+
+
+def test_saved_tape_argument_checks():
+    """Rejected on the host before any launch: a tape that is not 16-byte aligned, a null
+    tape, and meshes without the stored pair tables."""
+    import torch
+    import paper_2312_07874_gb300 as E
+    mesh, X, D, um = workload(2, 3, 2, True, "LF", "vortex")
+    gm = gpu_mesh(2, 2, X, mesh)
+    u = to_dev(um)
+    out, g = torch.empty_like(u), torch.empty_like(u)
+    n = E.esd_tape_doubles(gm.handle)
+    assert n % 32 == 0
+    buf = torch.empty(n + 1, dtype=torch.float64, device="cuda")
+    with pytest.raises(RuntimeError, match="16-byte"):
+        E.esd_rhs_save(gm.handle, u, out, buf[1:])
+    with pytest.raises(RuntimeError, match="16-byte"):
+        E.esd_rhs_vjp_saved(gm.handle, u, buf[1:], u, g)
+    otf = E.Mesh(2, 2, X, mesh.nbr_elem, mesh.nbr_face, metrics_on_the_fly=True)
+    with pytest.raises(RuntimeError, match="pair tables"):
+        E.esd_rhs_save(otf.handle, u, out, buf[:n])
+    torch.cuda.synchronize()
