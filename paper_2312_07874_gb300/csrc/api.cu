@@ -1157,7 +1157,7 @@ esd_status esd_autotune_kernels(esd_mesh m, const double* u, int kernels, void* 
       if (e == 1) break;
     }
   }
-  // residual: elements per CTA (threads follow: E * line tasks rounded to warps)
+  // residual: elements per CTA (threads follow: E * line tasks * lanes per task, rounded to warps)
   if (kernels & ESD_TUNE_RESIDUAL) {
     cudaError_t e0 = launch_project(m->R, m->M, best, u, nullptr, s);
     if (e0) return cuda_fail(e0, "autotune projection");
@@ -1165,11 +1165,12 @@ esd_status esd_autotune_kernels(esd_mesh m, const double* u, int kernels, void* 
     ep.mode = 0;
     ep.dudt = m->ws_stage;   // scratch output (the RK stage buffer; autotuning drops captured graphs)
     float tbest = 1e30f;
-    const int emax = std::min(std::max(1, (int)(budget / smem_residual(r, 1))), std::max(1, 1024 / r.T));
+    const int emax = std::min(std::max(1, (int)(budget / smem_residual(r, 1))),
+                              std::max(1, 1024 / (residual_line_lanes(r.dim, r.n) * r.T)));
     for (int e = 1; e <= emax; ++e) {
       LaunchCfg L = best;
       L.eb = e;
-      L.tb = std::max(64, ((e * r.T + 31) / 32) * 32);
+      L.tb = residual_threads(r.dim, r.n, r.T, e);
       L.sb = smem_residual(r, e);
       float t = time_launches([&] { return launch_residual(m->R, m->M, L, ep, s); }, s, 3);
       if (verbose) std::fprintf(stderr, "esd_autotune: residual elems/CTA %3d threads %4d  %.4f ms\n", e, L.tb, t);

@@ -761,10 +761,11 @@ __device__ __forceinline__ void line_task_shared(int ph, int t, bool act, const 
     else { base = t; stride = N * N; }
   }
   // Node residuals of the line: in registers (acc, unrolled pair loops), or -- where N
-  // accumulators no longer fit in registers beside the flux (tetrahedra N >= 6, triangles
-  // N >= 8) -- directly in the shared residual r, which this task owns for its line in
-  // this phase, with node a's running sum over its pairs in registers.
-  constexpr bool SACC = D == 3 ? N >= 6 : N >= 8;
+  // accumulators no longer fit in registers beside the flux (tetrahedra N >= 6), or where
+  // the register path's ~240 registers would cap triangles at 8 warps per SM (N >= 5) --
+  // directly in the shared residual r, which this task owns for its line in this phase,
+  // with node a's running sum over its pairs in registers (about 96 registers).
+  constexpr bool SACC = D == 3 ? N >= 6 : N >= 5;
   double acc[N][NC];
   if constexpr (!SACC) {
 #pragma unroll
@@ -973,6 +974,245 @@ __device__ __forceinline__ void line_task_shared(int ph, int t, bool act, const 
   }
 }
 
+// Tetrahedra with N >= 8: one element's tile (72-175 KB) leaves 1-2 warps per SM scheduler,
+// too few to hide the FP64 latency of one line task per thread.  Here two threads (adjacent
+// lanes, h = 0, 1) share each line task, accumulating in the shared residual r:
+//  * volume pairs in round-robin rounds: with MO = N (N odd) or N + 1 (a dummy node), round s
+//    holds the pairs {i, j} with i + j = s (mod MO) -- every node in at most one pair, every
+//    pair in exactly one round -- and the round's pairs alternate between the two threads;
+//    __syncwarp() between rounds orders the two threads' updates of a node;
+//  * facet pairs split by the parity of the line node (each thread updates only its own
+//    nodes), the facet node's two partial sums combined by a lane exchange (p0 + p1 in both
+//    lanes, so both hold the same value);
+//  * interface fluxes computed by one lane and exchanged.
+// Every thread of the block calls this (the rounds, lane exchanges and the facet-4 steps
+// synchronise); `act` marks the threads that own a task.
+// threads per line task of the residual kernel (the host's residual_line_lanes gives the same)
+template <int D, int N>
+constexpr int kLineLanes = (D == 3 && N >= 8) ? 2 : 1;
+
+template <int D, int N>
+struct LineRounds {
+  static constexpr int MO = (N % 2) ? N : N + 1;   // odd slot count
+  static constexpr int HALF = (MO - 1) / 2;        // pairs per round (with the dummy)
+  static constexpr int INV2 = (MO + 1) / 2;        // 2 * INV2 = 1 (mod MO)
+};
+
+template <int D, int N, bool OTF>
+__device__ __forceinline__ void line_task_split(int ph, int t, int h, bool act, const DevRef& R, const DevMesh& M,
+                                                int64_t eg, const double* __restrict__ Sv,
+                                                const double* __restrict__ Sf, double* r, double* h4,
+                                                const double* __restrict__ vdir, const double* __restrict__ fdir,
+                                                const FluxK& K) {
+  static_assert(D == 3, "two threads per line task: tetrahedra");
+  constexpr int NC = D + 2;
+  using RR = LineRounds<D, N>;
+  const double* __restrict__ G = OTF ? M.gvol + eg * (int64_t)D * D * R.Nq : nullptr;
+  const double* __restrict__ JN = OTF ? M.jnf + eg * (int64_t)D * R.Nfn : nullptr;
+  auto jn_at = [&](int f, double* jn) {
+#pragma unroll
+    for (int m = 0; m < D; ++m) jn[m] = JN[m * R.Nfn + f];
+  };
+  const int Nq = R.Nq, Nfn = R.Nfn, Nqf = R.Nqf, T = R.T, Ntot = R.Ntot;
+  const unsigned full = 0xffffffffu;
+  const int lane0 = (threadIdx.x & 31) & ~1;   // the task's first lane
+  int base, stride;
+  if (ph == 0) { base = N * t; stride = 1; }
+  else if (ph == 1) { base = (t % N) + N * N * (t / N); stride = N; }
+  else { base = t; stride = N * N; }
+  auto node = [&](int a) { return base + a * stride; };
+  // facet pairs of facet node f (state Sj) with this thread's line nodes a = h, h + 2, ...:
+  // r[a] -= F, part -= F
+  auto strip = [&](const NodeState<D>& Sj, auto&& dir, double* part) {
+#pragma unroll 1
+    for (int a = h; a < N; a += 2) {
+      const NodeState<D> Si = load_state<D>(Sv, Ntot, node(a));
+      double nh[D], F[NC];
+      dir(a, nh);
+      ec_flux_fast<D>(Si, Sj, nh, K, F);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        r[c * Nq + node(a)] -= F[c];
+        part[c] -= F[c];
+      }
+    }
+  };
+  auto combine = [&](double* part) {   // part := p0 + p1 in both lanes
+#pragma unroll
+    for (int c = 0; c < NC; ++c) part[c] += __shfl_xor_sync(full, part[c], 1);
+  };
+  auto lift = [&](const double* l, const double* hs) {   // r[a] -= l[a] hs for this thread's a
+#pragma unroll 1
+    for (int a = h; a < N; a += 2) {
+      const double la = l[a];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        double& ra = r[c * Nq + node(a)];
+        ra = fma(-la, hs[c], ra);
+      }
+    }
+  };
+  // 1. volume pairs, round by round
+  constexpr int Lv = N * (N - 1) / 2;
+  const double* vd = act && !OTF ? vdir + (size_t)ph * Lv * D * T + t : nullptr;
+#pragma unroll 1
+  for (int s = 0; s < RR::MO; ++s) {
+    if (act) {
+      const int u = (s * RR::INV2) % RR::MO;   // the node without a pair in this round
+#pragma unroll 1
+      for (int d = 1 + ((h + s) & 1); d <= RR::HALF; d += 2) {
+        int i = u + d, j = u - d;
+        if (i >= RR::MO) i -= RR::MO;
+        if (j < 0) j += RR::MO;
+        if (i >= N || j >= N) continue;   // the dummy node of even N
+        const int a = i < j ? i : j, b = i < j ? j : i;
+        const int m = a * (2 * N - a - 1) / 2 + (b - a - 1);   // the pair's index in the line's table
+        const NodeState<D> Si = load_state<D>(Sv, Ntot, node(a));
+        const NodeState<D> Sj = load_state<D>(Sv, Ntot, node(b));
+        double nh[D], F[NC];
+        if constexpr (OTF) {
+          otf_vol_dir<D>(R, G, Nq, ph, a, b, node(a), node(b), nh);
+        } else {
+#pragma unroll
+          for (int k = 0; k < D; ++k) nh[k] = vd[(m * D + k) * T];
+        }
+        ec_flux_fast<D>(Si, Sj, nh, K, F);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          r[c * Nq + node(a)] -= F[c];
+          r[c * Nq + node(b)] += F[c];
+        }
+      }
+    }
+    __syncwarp();
+  }
+  // 2. facets attached to the line
+  if (ph == 0) {
+    // faces 2 and 3 (f = (1 + zz) Nqf + t): lane h computes the interface flux of face 2 + h
+    double own[NC];
+    const int fo = (1 + h) * Nqf + t;
+    if (act) {
+      interface_flux<D>(M, Nq, Nfn, Ntot, eg, fo, Sf, K, own);
+    } else {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) own[c] = 0.0;
+    }
+#pragma unroll 1
+    for (int zz = 0; zz < 2; ++zz) {
+      double hs[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const double v = __shfl_sync(full, own[c], lane0 + zz);
+        hs[c] = h == 0 ? v : 0.0;   // lane 0 carries B J f*, lane 1 only its pair sums
+      }
+      if (act) {
+        const int f = (1 + zz) * Nqf + t;
+        const NodeState<D> Sj = load_state<D>(Sf, Ntot, f);
+        const double* l = zz == 0 ? R.l1p : R.l1m;
+        if constexpr (OTF) {
+          double jn[D];
+          jn_at(f, jn);
+          const double wq = 0.25 * R.wfac[f];
+          strip(Sj, [&](int a, double* nh) { otf_fac_dir<D>(G, Nq, R.nhat[1 + zz], node(a), jn, wq * l[a], nh); },
+                hs);
+        } else {
+          const double* fd = fdir + R.fph_off[0] + (size_t)zz * N * D * T + t;
+          strip(Sj, [&](int a, double* nh) {
+#pragma unroll
+            for (int k = 0; k < D; ++k) nh[k] = fd[(a * D + k) * T];
+          }, hs);
+        }
+      }
+      combine(hs);
+      if (act) lift(zz == 0 ? R.l1p : R.l1m, hs);
+    }
+  } else if (ph == 1) {
+    // face 1 (f = t): lane 0 computes the interface flux
+    const int f = t;
+    double own[NC], hs[NC];
+    if (act && h == 0) {
+      interface_flux<D>(M, Nq, Nfn, Ntot, eg, f, Sf, K, own);
+    } else {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) own[c] = 0.0;
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) hs[c] = own[c];
+    if (act) {
+      const NodeState<D> Sj = load_state<D>(Sf, Ntot, f);
+      if constexpr (OTF) {
+        double jn[D];
+        jn_at(f, jn);
+        const double wq = 0.25 * R.wfac[f];
+        strip(Sj, [&](int a, double* nh) { otf_fac_dir<D>(G, Nq, R.nhat[0], node(a), jn, wq * R.l2m[a], nh); }, hs);
+      } else {
+        const double* fd = fdir + R.fph_off[1] + t;
+        strip(Sj, [&](int a, double* nh) {
+#pragma unroll
+          for (int k = 0; k < D; ++k) nh[k] = fd[(a * D + k) * T];
+        }, hs);
+      }
+    }
+    combine(hs);
+    if (act) lift(R.l2m, hs);
+  } else {
+    // face 4: h4 = B J f* of node t (lane 0), then N barrier-separated steps of the diagonal
+    // schedule (task (a1, a2) handles column b' = (a2 + k) mod N), then the lift along the
+    // eta3-line
+    if (act && h == 0) {
+      double hs[NC];
+      interface_flux<D>(M, Nq, Nfn, Ntot, eg, 3 * Nqf + t, Sf, K, hs);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) h4[c * Nqf + t] = hs[c];
+    }
+    __syncthreads();
+    const int a1 = t % N, a2 = t / N;
+    const double* fd4 = (act && !OTF) ? fdir + R.fph_off[3] + t : nullptr;
+#pragma unroll 1
+    for (int k = 0; k < N; ++k) {
+      const int bp = a2 + k < N ? a2 + k : a2 + k - N;
+      const int j = a1 + N * bp;
+      double hs[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) hs[c] = 0.0;
+      if (act) {
+        const NodeState<D> Sj = load_state<D>(Sf, Ntot, 3 * Nqf + j);
+        if constexpr (OTF) {
+          double jn[D];
+          jn_at(3 * Nqf + j, jn);
+          const double wq = 0.25 * R.wfac[3 * Nqf + j] * R.L2J[bp * N + a2];
+          strip(Sj, [&](int a, double* nh) { otf_fac_dir<D>(G, Nq, R.nhat[3], node(a), jn, wq * R.l3m[a], nh); },
+                hs);
+        } else {
+          const double* fd = fd4 + (size_t)bp * N * D * T;
+          strip(Sj, [&](int a, double* nh) {
+#pragma unroll
+            for (int kk = 0; kk < D; ++kk) nh[kk] = fd[(a * D + kk) * T];
+          }, hs);
+        }
+      }
+      combine(hs);
+      if (act && h == 0) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) h4[c * Nqf + j] += hs[c];
+      }
+      __syncthreads();
+    }
+    if (act) {   // y = sum_b' L2J[b'][a2] h4(a1, b'), lifted along the eta3-line
+      double y[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) y[c] = 0.0;
+#pragma unroll 1
+      for (int bp = 0; bp < N; ++bp) {
+        const double w = R.L2J[bp * N + a2];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) y[c] = fma(w, h4[c * Nqf + a1 + N * bp], y[c]);
+      }
+      lift(R.l3m, y);
+    }
+  }
+}
+
 // Line task t of phase ph (Section 5.1, along collapsed-coordinate lines, Remark 4): the
 // pairs of one eta_{ph+1}-line of N nodes, the facet nodes attached to it -- their
 // interface fluxes, facet-correction pairs and lift -- accumulated in registers.
@@ -993,9 +1233,9 @@ __device__ __forceinline__ void line_task(int ph, int t, bool act, const DevRef&
                                           double* h4, const double* __restrict__ vdir,
                                           const double* __restrict__ fdir, const FluxK& K) {
   constexpr int NC = D + 2;
-  // Where N accumulators no longer fit in registers beside the flux (tetrahedra N >= 6,
-  // triangles N >= 8) the line's residuals accumulate in shared memory instead.
-  if constexpr (D == 3 ? N >= 6 : N >= 8) {
+  // Tetrahedra N >= 6 (N accumulators no longer fit in registers beside the flux) and
+  // triangles N >= 5 (occupancy): the line's residuals accumulate in shared memory instead.
+  if constexpr (D == 3 ? N >= 6 : N >= 5) {
     line_task_shared<D, N, OTF>(ph, t, act, R, M, eg, Sv, Sf, r, h4, vdir, fdir, K);
     return;
   }
@@ -1215,7 +1455,9 @@ __device__ void residual_tile(const DevRef& R, const DevMesh& M, int64_t e0, int
   //    (Eq. (entropy_stable)), one line task per thread and phase
   {
     const FluxK K = make_fluxk(M.gamma);
-    const int el = threadIdx.x / T, t = threadIdx.x % T;
+    constexpr int LPL = kLineLanes<D, N>;   // threads per line task
+    const int task = (int)threadIdx.x / LPL, h = (int)threadIdx.x % LPL;
+    const int el = task / T, t = task % T;
     const bool act = el < E;
     const int elc = act ? el : 0;
     const int64_t eg = e0 + elc;
@@ -1224,8 +1466,12 @@ __device__ void residual_tile(const DevRef& R, const DevMesh& M, int64_t e0, int
     double* base = sm + elc * pe;
 #pragma unroll 1
     for (int ph = 0; ph < D; ++ph) {
-      line_task<D, N, OTF>(ph, t, act, R, M, eg, base + Ly.oS, base + Ly.oS + Nq, base + Ly.oR, base + Ly.oH4, vdir,
-                           fdir, K);
+      if constexpr (LPL == 2)
+        line_task_split<D, N, OTF>(ph, t, h, act, R, M, eg, base + Ly.oS, base + Ly.oS + Nq, base + Ly.oR,
+                                   base + Ly.oH4, vdir, fdir, K);
+      else
+        line_task<D, N, OTF>(ph, t, act, R, M, eg, base + Ly.oS, base + Ly.oS + Nq, base + Ly.oR, base + Ly.oH4,
+                             vdir, fdir, K);
       __syncthreads();
     }
   }

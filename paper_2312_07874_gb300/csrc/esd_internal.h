@@ -170,6 +170,14 @@ cudaError_t launch_l2_project(const DevRef& R, const DevMesh& M, const double* u
 // (a tape saved by the forward call), so the projection kernel is not launched again
 cudaError_t launch_vjp(const DevRef& R, const DevMesh& M, const LaunchCfg& L, const double* u, const double* cot,
                        double* grad, double* qbar, double* qext, cudaStream_t s, bool project_first = true);
+// threads per line task of the residual kernel: 2 for tetrahedra with N = p + 1 >= 8
+// (device.cuh: kLineLanes, line_task_split), else 1; a residual block needs
+// residual_threads(dim, n, T, e) threads for e elements of T line tasks each
+inline int residual_line_lanes(int dim, int n) { return dim == 3 && n >= 8 ? 2 : 1; }
+inline int residual_threads(int dim, int n, int T, int e) {
+  const int w = (residual_line_lanes(dim, n) * e * T + 31) / 32 * 32;
+  return w > 64 ? w : 64;
+}
 cudaError_t launch_residual_adjoint(const DevRef& R, const DevMesh& M, const LaunchCfg& L, const double* cot,
                                     double* qbar, double* qext, cudaStream_t s);
 cudaError_t launch_project_adjoint(const DevRef& R, const DevMesh& M, const LaunchCfg& L, const double* u,

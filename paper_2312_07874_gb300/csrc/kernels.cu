@@ -566,25 +566,26 @@ LaunchCfg choose_launch(const RefTables& r) {
   // residual: E*T threads for the pair phases.  The kernels use up to ~255 registers, so an SM
   // holds at most 256 of their threads; pick E to maximise the threads doing pair work per SM
   // (CTAs per SM x E*T, limited by shared memory and registers), then lane utilisation.
+  const int lanes = residual_line_lanes(r.dim, r.n);
   int emax = std::max(1, (int)(kSmemBudget / smem_residual(r, 1)));
-  emax = std::min(emax, 1024 / r.T);
+  emax = std::min(emax, std::max(1, 1024 / (lanes * r.T)));
   int best = 1;
   double best_score = -1.0;
   for (int e = 1; e <= emax; ++e) {
-    const int thr = ((e * r.T + 31) / 32) * 32;
+    const int thr = residual_threads(r.dim, r.n, r.T, e);
     const int by_smem = (int)(kSmemBudget / smem_residual(r, e));
     const int by_regs = std::max(1, 256 / thr);
     const int ctas = std::max(1, std::min(by_smem, by_regs));
     if (thr > 256 && e > 1) break;
-    const double useful = (double)ctas * e * r.T;   // lanes with pair work per SM
-    const double score = useful + 1e-3 * (double)(e * r.T) / thr;
+    const double useful = (double)ctas * e * r.T * lanes;   // lanes with pair work per SM
+    const double score = useful + 1e-3 * (double)(e * r.T * lanes) / thr;
     if (score > best_score) {
       best_score = score;
       best = e;
     }
   }
   L.eb = best;
-  L.tb = std::max(64, ((best * r.T + 31) / 32) * 32);
+  L.tb = residual_threads(r.dim, r.n, r.T, best);
   L.sb = smem_residual(r, best);
   // residual adjoint: same task structure, larger shared footprint
   // (the adjoint kernel uses up to 128 registers per thread: at most 512 threads per block)
@@ -635,7 +636,8 @@ bool audit_layouts(std::string* err) {
       const LaunchCfg C = choose_launch(r);
       if (smem_residual(r, C.eb) > kSmemBudget || smem_project(r, C.ea) > kSmemBudget)
         return bad(dim, p, "default shape exceeds the shared-memory budget");
-      if (C.tb < C.eb * r.T || C.tb > 1024 || C.tb % 32) return bad(dim, p, "residual threads");
+      if (C.tb < C.eb * r.T * residual_line_lanes(r.dim, r.n) || C.tb > 1024 || C.tb % 32)
+        return bad(dim, p, "residual threads");
       // residual adjoint
       const AdjLayout A = dim == 2 ? adj_layout<2>(r.Nq, r.Nfn, r.Np, r.n) : adj_layout<3>(r.Nq, r.Nfn, r.Np, r.n);
       if ((size_t)A.pe * 8 > kSmemBudget) return bad(dim, p, "adjoint footprint");
