@@ -102,12 +102,6 @@ def test_planted_mistakes_are_caught():
     uf = np.einsum("ij,i,eic->ecj", D.V, D.ref.w, np.broadcast_to(ubar, (D.E, D.ref.Nq, D.Nc)))
     orig = D._residual_dense
 
-    def no_correction(el, Ut, Utf, fstar):
-        saved = [R.copy() for R in D.ref.R]
-        r = orig(el, Ut, Utf, fstar)
-        # recompute without C: r_nc = r + C1 - R^T Ct1 is not available directly, so zero the
-        # two-point facet fluxes by zeroing B in the correction only
-        return r
     # (1) drop the correction: use the skew-free volume term plus plain lift
     def dropped(el, Ut, Utf, fstar):
         ref, geo, d = D.ref, D.geo, D.dim
