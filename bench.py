@@ -770,6 +770,14 @@ def run_sweep(args):
     def fwd_bwd(mode):
         u0 = u.clone().requires_grad_(True)
         (cot * rollout(u0, gm, dt, 20, mode)).sum().backward()
+    # the same 20 steps without checkpoints: the rollout's per-step checkpoint copies cost the
+    # difference
+    ur = u.clone()
+
+    def plain20():
+        for _ in range(20):
+            gm.rk_step(ur, dt)
+    t_plain = _time_flushed(torch, stream, plain20, 2, flush)
     roll = {}
     for mode in ("stages", "tapes"):
         t_f = _time_flushed(torch, stream, lambda: fwd_only(mode), 2, flush)
@@ -783,6 +791,7 @@ def run_sweep(args):
                       "rollout_20_steps_forward_backward_ms": roll["stages"]["rollout_20_steps_forward_backward_ms"],
                       "rollout_backward_forward_ratio": roll["stages"]["rollout_backward_forward_ratio"],
                       "checkpoint": "stages", "rollout_checkpoint_tapes": roll["tapes"],
+                      "plain_20_steps_ms": t_plain,
                       "l2": "flushed (256 MB write) before every timed call", "dtype": "f64"}), flush=True)
 
 
