@@ -977,10 +977,11 @@ __device__ __forceinline__ void line_task_shared(int ph, int t, bool act, const 
 // Tetrahedra with N >= 8: one element's tile (72-175 KB) leaves 1-2 warps per SM scheduler,
 // too few to hide the FP64 latency of one line task per thread.  Here two threads (adjacent
 // lanes, h = 0, 1) share each line task, accumulating in the shared residual r:
-//  * volume pairs in round-robin rounds: with MO = N (N odd) or N + 1 (a dummy node), round s
-//    holds the pairs {i, j} with i + j = s (mod MO) -- every node in at most one pair, every
-//    pair in exactly one round -- and the round's pairs alternate between the two threads;
-//    __syncwarp() between rounds orders the two threads' updates of a node;
+//  * volume pairs in round-robin rounds (the circle method): with MO = N (N odd) or N - 1
+//    (N even), round s leaves out node u (2u = s mod MO) and pairs u + d with u - d (mod MO),
+//    d = 1 .. (MO - 1) / 2, and for even N also u with node N - 1 -- every node in at most one
+//    pair, every pair in exactly one round; the round's pairs alternate between the two
+//    threads, and __syncwarp() between rounds orders the two threads' updates of a node;
 //  * facet pairs split by the parity of the line node (each thread updates only its own
 //    nodes), the facet node's two partial sums combined by a lane exchange (p0 + p1 in both
 //    lanes, so both hold the same value);
@@ -993,8 +994,10 @@ constexpr int kLineLanes = (D == 3 && N >= 8) ? 2 : 1;
 
 template <int D, int N>
 struct LineRounds {
-  static constexpr int MO = (N % 2) ? N : N + 1;   // odd slot count
-  static constexpr int HALF = (MO - 1) / 2;        // pairs per round (with the dummy)
+  static constexpr bool EVEN = N % 2 == 0;
+  static constexpr int MO = EVEN ? N - 1 : N;      // odd circle; node N - 1 of even N stays fixed
+  static constexpr int HALF = (MO - 1) / 2;        // circle pairs per round
+  static constexpr int D0 = EVEN ? 0 : 1;          // d = 0: the pair (u, N - 1) of even N
   static constexpr int INV2 = (MO + 1) / 2;        // 2 * INV2 = 1 (mod MO)
 };
 
@@ -1058,13 +1061,19 @@ __device__ __forceinline__ void line_task_split(int ph, int t, int h, bool act, 
 #pragma unroll 1
   for (int s = 0; s < RR::MO; ++s) {
     if (act) {
-      const int u = (s * RR::INV2) % RR::MO;   // the node without a pair in this round
+      const int u = (s * RR::INV2) % RR::MO;   // left out of the circle pairs in this round
 #pragma unroll 1
-      for (int d = 1 + ((h + s) & 1); d <= RR::HALF; d += 2) {
-        int i = u + d, j = u - d;
-        if (i >= RR::MO) i -= RR::MO;
-        if (j < 0) j += RR::MO;
-        if (i >= N || j >= N) continue;   // the dummy node of even N
+      for (int d = RR::D0 + ((h + s) & 1); d <= RR::HALF; d += 2) {
+        int i, j;
+        if (d == 0) {   // even N: u with the fixed node
+          i = u;
+          j = N - 1;
+        } else {
+          i = u + d;
+          j = u - d;
+          if (i >= RR::MO) i -= RR::MO;
+          if (j < 0) j += RR::MO;
+        }
         const int a = i < j ? i : j, b = i < j ? j : i;
         const int m = a * (2 * N - a - 1) / 2 + (b - a - 1);   // the pair's index in the line's table
         const NodeState<D> Si = load_state<D>(Sv, Ntot, node(a));
