@@ -99,6 +99,7 @@ SYMBOLS = {
     "esd_debug_math": ([ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p],
                        ctypes.c_int),
     "esd_debug_set_mesh_device": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
+    "esd_debug_batch_solo_waves": ([ctypes.c_int], ctypes.c_int),
     "esd_skew_create": ([ctypes.POINTER(esd_mesh_desc), ctypes.POINTER(esd_skew_model),
                          ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
     "esd_skew_destroy": ([ctypes.c_void_p], ctypes.c_int),

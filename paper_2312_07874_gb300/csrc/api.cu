@@ -748,9 +748,21 @@ esd_status esd_part_import(esd_mesh m, int kind, const double* buf, int64_t firs
   return e ? cuda_fail(e, "trace import launch") : ESD_OK;
 }
 
+// A mesh whose residual launch fills the GPU for at least this many waves on its own runs
+// with its own launches inside the batch graph (see esd_batch_create); tests change it
+// through esd_debug_batch_solo_waves.
+static int g_batch_solo_waves = 4;
+
+esd_status esd_debug_batch_solo_waves(int waves) {
+  if (waves < 0) return fail(ESD_ERR_ARG, "waves must be >= 0");
+  g_batch_solo_waves = waves;
+  return ESD_OK;
+}
+
 struct BatchGroup {
   int dim = 0, p = 0;
-  std::vector<int> members;          // indices into the batch's mesh list
+  std::vector<int> members;          // indices into the batch's mesh list (persistent launches)
+  std::vector<int> solo;             // large meshes of the group, launched on their own
   std::vector<BatchItem> pitems, ritems;
   BatchItem* d_pitems = nullptr;
   BatchItem* d_ritems = nullptr;
@@ -814,6 +826,16 @@ esd_status esd_batch_create(const esd_mesh* meshes, int n, esd_batch* out) {
     for (int i = 0; i < n; ++i) {
       if (meshes[i]->dim != dim || meshes[i]->p != deg) continue;
       esd_mesh m = meshes[i];
+      // A mesh that fills the GPU for several waves gains nothing from the persistent
+      // launch (its tail is a small part of its time) and loses to it: the persistent kernel
+      // reads each mesh's tables through global memory, where a mesh's own launch has them
+      // as kernel parameters.  Such meshes run their own launches in the group's branch.
+      const int64_t ctas = (m->E + m->L.eb - 1) / m->L.eb;
+      const int64_t per_sm = std::max<int64_t>(1, (int64_t)(227 * 1024) / (int64_t)std::max<size_t>(m->L.sb, 1));
+      if (ctas >= (int64_t)g_batch_solo_waves * sms * per_sm) {
+        g.solo.push_back(i);
+        continue;
+      }
       const int mi = (int)g.members.size();
       g.members.push_back(i);
       for (int64_t e0 = 0; e0 < m->E; e0 += m->L.ea)
@@ -825,7 +847,11 @@ esd_status esd_batch_create(const esd_mesh* meshes, int n, esd_batch* out) {
       g.pthreads = std::max(g.pthreads, m->L.ta);
       g.rthreads = std::max(g.rthreads, m->L.tb);
     }
-    if (g.members.empty()) continue;
+    if (g.members.empty() && g.solo.empty()) continue;
+    if (g.members.empty()) {   // only large meshes: no persistent launch
+      b->groups.push_back(g);
+      continue;
+    }
     // largest items first so that the persistent grid finishes evenly
     auto by_cost = [&](const BatchItem& x, const BatchItem& y) {
       const esd_mesh mx = meshes[g.members[x.mesh]], my = meshes[g.members[y.mesh]];
@@ -873,6 +899,10 @@ static cudaError_t batch_sequence(esd_batch b, BatchGraph& G, cudaStream_t s) {
   cudaError_t e;
   for (int st = 0; st < nst; ++st) {
     for (auto& g : b->groups) {
+      if (g.members.empty()) {   // no persistent launch in this group
+        G.d_tables.push_back(nullptr);
+        continue;
+      }
       std::vector<BatchMesh> tab(g.members.size());
       for (size_t k = 0; k < g.members.size(); ++k) {
         const int i = g.members[k];
@@ -965,11 +995,37 @@ static esd_status batch_run(esd_batch b, int kind, const std::vector<const doubl
     if ((e1 = cudaStreamWaitEvent(gs[gi], ev[ng], 0))) break;
     for (int st = 0; st < nst && !e1; ++st) {
       BatchMesh* tab = G.d_tables[st * ng + gi];
-      if ((e1 = launch_batch(g.dim, g.p + 1, 0, tab, g.d_pitems, (int)g.pitems.size(), g.pgrid, g.pthreads,
-                             g.psmem, gs[gi])))
-        break;
-      e1 = launch_batch(g.dim, g.p + 1, 1, tab, g.d_ritems, (int)g.ritems.size(), g.rgrid, g.rthreads, g.rsmem,
-                        gs[gi]);
+      if (!g.members.empty()) {
+        if ((e1 = launch_batch(g.dim, g.p + 1, 0, tab, g.d_pitems, (int)g.pitems.size(), g.pgrid, g.pthreads,
+                               g.psmem, gs[gi])))
+          break;
+        if ((e1 = launch_batch(g.dim, g.p + 1, 1, tab, g.d_ritems, (int)g.ritems.size(), g.rgrid, g.rthreads,
+                               g.rsmem, gs[gi])))
+          break;
+      }
+      for (int i : g.solo) {   // the group's large meshes: their own launches, same stage
+        esd_mesh m = b->meshes[i];
+        double* u = const_cast<double*>(G.u[i]);
+        const double* in = u;
+        Epilogue ep{};
+        if (kind == 0) {
+          ep.mode = 0;
+          ep.dudt = const_cast<double*>(G.u[b->meshes.size() + i]);
+        } else {
+          const double ra[4] = {0.5, 0.5, 1.0, 0.0};
+          const double rb[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+          in = st == 0 ? u : m->ws_stage;
+          ep.mode = 1;
+          ep.u0 = u;
+          ep.acc_in = st == 0 ? u : m->ws_acc;
+          ep.acc_out = st == 3 ? u : m->ws_acc;
+          ep.stage_out = st == 3 ? nullptr : m->ws_stage;
+          ep.ca = ra[st] * G.dt[i];
+          ep.cb = rb[st] * G.dt[i];
+        }
+        if ((e1 = launch_project(m->R, m->M, m->L, in, nullptr, gs[gi]))) break;
+        if ((e1 = launch_residual(m->R, m->M, m->L, ep, gs[gi]))) break;
+      }
     }
     if (!e1) e1 = cudaEventRecord(ev[gi], gs[gi]);
     if (!e1) e1 = cudaStreamWaitEvent(cs, ev[gi], 0);

@@ -126,6 +126,41 @@ def test_batch_rk_step_equals_per_mesh():
     E.esd_batch_destroy(b)
 
 
+@pytest.mark.parametrize("waves", [0, 1])
+def test_batch_with_meshes_on_their_own_launches(waves):
+    """Large members of a batch run their own launches inside the batch graph (waves = 0:
+    every mesh; waves = 1: the meshes whose residual launch fills a wave, next to the
+    persistent launches of the others): d u~/dt and the RK4 step stay bitwise equal to the
+    per-mesh path."""
+    import torch
+    import paper_2312_07874_gb300 as E
+    ms = _meshes()
+    E.lib().esd_debug_batch_solo_waves(waves)
+    try:
+        b = E.esd_batch_create([m.handle for m, _ in ms])
+    finally:
+        E.lib().esd_debug_batch_solo_waves(4)
+    outs = [torch.empty_like(u) for _, u in ms]
+    E.esd_batch_rhs(b, [u for _, u in ms], outs)
+    torch.cuda.synchronize()
+    for (m, u), o in zip(ms, outs):
+        assert torch.equal(o, m.rhs(u))
+    ua = [u.clone() for _, u in ms]
+    ub = [u.clone() for _, u in ms]
+    dts = [0.1 * (2 * np.pi / M) / (12.0 * (2 * p + 1)) for (_, M, p, _) in MIX]
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        for _ in range(2):
+            E.esd_batch_rk_step(b, ua, dts)
+            for (m, _), u, dt in zip(ms, ub, dts):
+                m.rk_step(u, dt)
+    s.synchronize()
+    for a, c in zip(ua, ub):
+        assert torch.equal(a, c)
+    E.esd_batch_destroy(b)
+    assert E.lib().esd_debug_batch_solo_waves(-1) != 0
+
+
 def test_autotune_subset_and_invalid_bits():
     import torch
     import paper_2312_07874_gb300 as E
