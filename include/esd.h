@@ -331,7 +331,11 @@ esd_status esd_skew_check(esd_skew skew, void* stream);
 esd_status esd_skew_info(esd_skew skew, int* n_vars, int* elems_per_cta, int* threads_per_cta);
 
 /* Batched, persistent execution of many independent meshes (not in the paper).
- * The batch keeps references to the meshes, which must outlive it. */
+ * Meshes are grouped by (dim, p).  In each group, the meshes whose residual launch would not
+ * fill the GPU once share one persistent projection launch and one persistent residual
+ * launch per stage; larger meshes keep their own launches.  One CUDA graph holds all groups
+ * as concurrent branches.  Results equal the per-mesh calls bit for bit.  The batch keeps
+ * references to the meshes, which must outlive it. */
 esd_status esd_batch_create(const esd_mesh* meshes, int n, esd_batch* out);
 esd_status esd_batch_destroy(esd_batch batch);
 /* u[i], dudt[i]: device state arrays of mesh i (layouts as above). */

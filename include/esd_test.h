@@ -62,7 +62,7 @@ esd_status esd_debug_set_mesh_device(esd_mesh mesh, int device);
 
 /* Test hook: the size (in waves of residual CTAs over the GPU) from which esd_batch_create
  * runs a member mesh with its own launches inside the batch graph instead of the group's
- * persistent launch (default 4).  0 runs every mesh on its own; a large value runs every
+ * persistent launch (default 1).  0 runs every mesh on its own; a large value runs every
  * mesh in the persistent launches.  Applies to batches created afterwards; ESD_ERR_ARG if
  * negative. */
 esd_status esd_debug_batch_solo_waves(int waves);

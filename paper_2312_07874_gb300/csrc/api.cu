@@ -751,7 +751,7 @@ esd_status esd_part_import(esd_mesh m, int kind, const double* buf, int64_t firs
 // A mesh whose residual launch fills the GPU for at least this many waves on its own runs
 // with its own launches inside the batch graph (see esd_batch_create); tests change it
 // through esd_debug_batch_solo_waves.
-static int g_batch_solo_waves = 4;
+static int g_batch_solo_waves = 1;
 
 esd_status esd_debug_batch_solo_waves(int waves) {
   if (waves < 0) return fail(ESD_ERR_ARG, "waves must be >= 0");

@@ -126,12 +126,12 @@ def test_batch_rk_step_equals_per_mesh():
     E.esd_batch_destroy(b)
 
 
-@pytest.mark.parametrize("waves", [0, 1])
+@pytest.mark.parametrize("waves", [0, 1, 1000])
 def test_batch_with_meshes_on_their_own_launches(waves):
     """Large members of a batch run their own launches inside the batch graph (waves = 0:
-    every mesh; waves = 1: the meshes whose residual launch fills a wave, next to the
-    persistent launches of the others): d u~/dt and the RK4 step stay bitwise equal to the
-    per-mesh path."""
+    every mesh; waves = 1, the default: the meshes whose residual launch fills a wave, next
+    to the persistent launches of the others; 1000: every mesh in the persistent launches):
+    d u~/dt and the RK4 step stay bitwise equal to the per-mesh path."""
     import torch
     import paper_2312_07874_gb300 as E
     ms = _meshes()
@@ -139,7 +139,7 @@ def test_batch_with_meshes_on_their_own_launches(waves):
     try:
         b = E.esd_batch_create([m.handle for m, _ in ms])
     finally:
-        E.lib().esd_debug_batch_solo_waves(4)
+        E.lib().esd_debug_batch_solo_waves(1)
     outs = [torch.empty_like(u) for _, u in ms]
     E.esd_batch_rhs(b, [u for _, u in ms], outs)
     torch.cuda.synchronize()
