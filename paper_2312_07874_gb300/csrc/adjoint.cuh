@@ -8,11 +8,13 @@
 
 namespace esd {
 
-// the tables hold n/2; the adjoint works with the full direction
+// The tables hold n/2.  The pair adjoint's outputs are bilinear in the direction and the
+// cotangent F_b, so the residual adjoint keeps its cotangents r_b, h_b doubled instead and
+// uses n/2 as stored: the same values (scaling by 2 is exact), D multiplies fewer per pair.
 template <int D>
 __device__ __forceinline__ void load_dir(const double* base, int slot, int T, int t, double* n) {
 #pragma unroll
-  for (int k = 0; k < D; ++k) n[k] = 2.0 * base[(slot * D + k) * T + t];
+  for (int k = 0; k < D; ++k) n[k] = base[(slot * D + k) * T + t];
 }
 
 // ---------------------------------------------------------------------------
@@ -45,8 +47,9 @@ __device__ __forceinline__ void ec_flux_adj(const NodeState<D>& L, const NodeSta
   const double r1 = rcp_nr<1>(s1), f1 = d1 * r1, u1 = f1 * f1;
   const bool ser1 = below_logmean_cutoff(u1);
   const double G = fma(u1, fma(u1, fma(u1, -22.0 / 945.0, -2.0 / 45.0), -1.0 / 6.0), 0.5);
-  const double Gp = fma(u1, fma(u1, -22.0 / 315.0, -4.0 / 45.0), -1.0 / 6.0);
-  const double t1 = 4.0 * f1 * r1 * Gp;
+  // 4 G'(u) with the factor 4 in the coefficients (exact: a power of two)
+  const double Gp4 = fma(u1, fma(u1, 4.0 * (-22.0 / 315.0), 4.0 * (-4.0 / 45.0)), 4.0 * (-1.0 / 6.0));
+  const double t1 = f1 * r1 * Gp4;
   double rl = s1 * G, dra = fma(-t1, R.rho, G), drb = fma(t1, L.rho, G);
   if (__any_sync(active, !ser1)) {
     const double rln = rcp_nr<2>(R.lrho - L.lrho), m = d1 * rln;
@@ -61,8 +64,8 @@ __device__ __forceinline__ void ec_flux_adj(const NodeState<D>& L, const NodeSta
   const double r2 = rcp_nr<2>(s2), f2 = d2 * r2, u2 = f2 * f2;
   const bool ser2 = below_logmean_cutoff(u2);
   const double H = fma(u2, fma(u2, fma(u2, 2.0 / 7.0, 2.0 / 5.0), 2.0 / 3.0), 2.0);
-  const double Hp = fma(u2, fma(u2, 6.0 / 7.0, 4.0 / 5.0), 2.0 / 3.0);
-  const double t2 = 4.0 * f2 * r2 * Hp, r2s = r2 * r2;
+  const double Hp4 = fma(u2, fma(u2, 4.0 * (6.0 / 7.0), 4.0 * (4.0 / 5.0)), 4.0 * (2.0 / 3.0));   // 4 H'(u)
+  const double t2 = f2 * r2 * Hp4, r2s = r2 * r2;
   double ib = r2 * H, dia = -r2s * fma(t2, R.beta, H), dib = -r2s * fma(-t2, L.beta, H);
   if (__any_sync(active, !ser2)) {
     const double rd = rcp_nr<2>(d2), m = (R.lbeta - L.lbeta) * rd;
@@ -80,7 +83,8 @@ __device__ __forceinline__ void ec_flux_adj(const NodeState<D>& L, const NodeSta
     vnR = fma(n[k], R.v[k], vnR);
     vv = fma(L.v[k], R.v[k], vv);
   }
-  const double frho = rl * 0.5 * (vnL + vnR);
+  const double hvn = 0.5 * (vnL + vnR);
+  const double frho = rl * hvn, hfrho = 0.5 * frho;
   const double FE = Fb[D + 1];
   double frho_b = fma(FE, fma(0.5, vv, inv_gm1 * ib), Fb[0]);
   double pavg_b = 0.0;
@@ -94,13 +98,13 @@ __device__ __forceinline__ void ec_flux_adj(const NodeState<D>& L, const NodeSta
   const double ib_b = FE * frho * inv_gm1;
   double pL_b = fma(0.5, pavg_b, hFE * vnR);
   double pR_b = fma(0.5, pavg_b, hFE * vnL);
-  const double rl_b = frho_b * 0.5 * (vnL + vnR);
+  const double rl_b = frho_b * hvn;
   const double hfr = 0.5 * frho_b * rl;
   const double vnL_b = fma(hFE, R.p, hfr);
   const double vnR_b = fma(hFE, L.p, hfr);
 #pragma unroll
   for (int k = 0; k < D; ++k) {
-    const double vs_b = 0.5 * Fb[1 + k] * frho;
+    const double vs_b = Fb[1 + k] * hfrho;
     qL[1 + k] += fma(vnL_b, n[k], fma(vv_b, R.v[k], vs_b));
     qR[1 + k] += fma(vnR_b, n[k], fma(vv_b, L.v[k], vs_b));
   }

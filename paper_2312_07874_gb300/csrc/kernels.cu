@@ -152,11 +152,16 @@ __global__ void residual_adjoint_kernel(DevRef R, DevMesh M, int epc, const doub
   }
   __syncthreads();
   apply_V<D>(R, tile, Ly.oM, Ly.oS1, Ly.oS2, Ly.oRb, NC);
-  // 2. h_b = -R r_b  (r -= R^T h in the forward)
+  // 2. h_b = -R r_b  (r -= R^T h in the forward).  From here on r_b and h_b are held doubled
+  //    (the pair tables hold n/2; see load_dir), exactly: scaling by 2 rounds nothing.
   apply_R<D>(R, tile, Ly.oRb, Ly.oS1, Ly.oHb, NC);
   for (int idx = threadIdx.x; idx < E * NC * Nfn; idx += blockDim.x) {
     int e = idx / (NC * Nfn);
-    sm[e * pe + Ly.oHb + idx % (NC * Nfn)] *= -1.0;
+    sm[e * pe + Ly.oHb + idx % (NC * Nfn)] *= -2.0;
+  }
+  for (int idx = threadIdx.x; idx < E * NC * Nq; idx += blockDim.x) {
+    int e = idx / (NC * Nq);
+    sm[e * pe + Ly.oRb + idx % (NC * Nq)] *= 2.0;
   }
   // 3. states, zero cotangents
   for (int idx = threadIdx.x; idx < E * NF * Ntot; idx += blockDim.x) {
@@ -206,7 +211,7 @@ __global__ void residual_adjoint_kernel(DevRef R, DevMesh M, int epc, const doub
     double nn[D];
 #pragma unroll
     for (int k = 0; k < D; ++k) nn[k] = M.nrm[(eg * D + k) * Nfn + f];
-    const double bj = M.bj[eg * Nfn + f];
+    const double bj = 0.5 * M.bj[eg * Nfn + f];   // h_b is held doubled
     double fb[NC], qL[NQ], qR[NQ];
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
