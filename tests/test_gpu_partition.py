@@ -34,6 +34,7 @@ def _parts(dim, p, X, mesh, flux, kind, P):
     (2, 4, 3, "vortex", "EC", "round_robin", 3),
     (3, 3, 3, "tgv", "LF", "slab", 2),
     (3, 3, 4, "density_wave", "EC", "round_robin", 3),
+    (3, 3, 7, "tgv", "LF", "round_robin", 2),   # two lanes per line task (tetrahedra p >= 7)
 ])
 def test_split_mesh_matches_unsplit(dim, M, p, state, flux, kind, P):
     import torch

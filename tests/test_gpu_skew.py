@@ -73,6 +73,48 @@ def test_skew_euler_parity(dim, M, p, state, flux):
           n_exact=3 if p < 7 else 2, seed=p)
 
 
+@pytest.mark.parametrize("p", [8, 10])
+def test_skew_euler_high_degree_tets_sampled(p):
+    """Tetrahedra p = 8 and 10 (162 curved elements, the instantiations for N = 9 and 11):
+    two sampled elements against the skew oracle on their sub-mesh in FP64 and in long
+    double (evaluating the oracle on the whole mesh would take minutes at these degrees)."""
+    import torch
+    import paper_2312_07874_gb300 as E
+    mesh, X = I.config_mesh(3, 3, L, p, True)
+    gs = E.Skew(3, p, X, mesh.nbr_elem, mesh.nbr_face, model="euler", flux="LF")
+    rng = np.random.default_rng(p)
+    pick = np.sort(rng.choice(len(X), size=2, replace=False))
+    D64, need, local = extended.sub_discretization(3, p, X, mesh.nbr_elem, mesh.nbr_face, pick, flux="LF",
+                                                   dtype=float)
+    Dx, need_x, local_x = extended.sub_discretization(3, p, X, mesh.nbr_elem, mesh.nbr_face, pick, flux="LF")
+    assert np.array_equal(need, need_x) and np.array_equal(local, local_x)
+    # the state: a constant admissible state (its mode 0) plus seeded N(0, 1e-3) on every mode
+    # (the full-mesh projection of an analytic state would need the whole oracle mesh)
+    ubar = I.conservative_from_primitive(np.array(1.2), np.array([0.3, -0.2, 0.1]), np.array(1.5))
+    um = np.zeros((len(X), 5, D64.V.shape[1]))
+    um[:, :, 0] = np.asarray(ubar) / D64.V[0, 0]
+    um = np.ascontiguousarray(um + I.seeded_normal(200 + p, um.shape, 1e-3))
+    out = gs.rhs(to_dev(um))
+    torch.cuda.synchronize()
+    gs.check()
+    got = out.cpu().numpy()[pick]
+    om = skew.EulerModel(3, dissipation=True)
+    ref = skew.rhs(D64, um[need], om, "skew", local)
+    rx = skew.rhs(Dx, um[need].astype(extended.EXT), om, "skew", local)
+    e_gpu = np.asarray(rel_err_per_var(got, rx), dtype=float)
+    e_64 = np.asarray(rel_err_per_var(ref, rx), dtype=float)
+    e_flat = np.asarray(rel_err_per_var(got, ref), dtype=float)
+    flat = e_64 < FLAT_REACH
+    rec = dict(case=f"skew euler tet p={p} density_wave LF (sample)", e_gpu_exact=e_gpu.tolist(),
+               e_oracle64_exact=e_64.tolist(), e_gpu_oracle64=e_flat.tolist(), flat=flat.tolist(),
+               n_elems=int(len(pick)), n_exact=int(len(pick)))
+    _log(rec)
+    print(rec)
+    assert np.all(e_gpu <= C_EXACT * np.maximum(e_64, FLOOR)), ("accuracy vs exact", e_gpu, e_64)
+    assert np.all(e_gpu[flat] < PARITY_TOL), ("flat bound vs exact", e_gpu, e_64)
+    assert np.all(e_flat < 1e-9), ("against the FP64 oracle", e_flat)
+
+
 @pytest.mark.parametrize("dim,M,p", [(2, 3, 2), (2, 4, 5), (2, 3, 9), (3, 3, 2), (3, 3, 3), (3, 3, 5)])
 @pytest.mark.parametrize("upwind", [False, True])
 def test_skew_advection_parity(dim, M, p, upwind):
