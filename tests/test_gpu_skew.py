@@ -105,7 +105,7 @@ def test_skew_euler_high_degree_tets_sampled(p):
     e_64 = np.asarray(rel_err_per_var(ref, rx), dtype=float)
     e_flat = np.asarray(rel_err_per_var(got, ref), dtype=float)
     flat = e_64 < FLAT_REACH
-    rec = dict(case=f"skew euler tet p={p} density_wave LF (sample)", e_gpu_exact=e_gpu.tolist(),
+    rec = dict(case=f"skew euler tet p={p} constant + noise LF (sample)", e_gpu_exact=e_gpu.tolist(),
                e_oracle64_exact=e_64.tolist(), e_gpu_oracle64=e_flat.tolist(), flat=flat.tolist(),
                n_elems=int(len(pick)), n_exact=int(len(pick)))
     _log(rec)
