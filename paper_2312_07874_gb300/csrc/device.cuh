@@ -762,11 +762,11 @@ __device__ __forceinline__ void line_task_shared(int ph, int t, bool act, const 
   }
   // Node residuals of the line: in registers (acc, unrolled pair loops), or -- where N
   // accumulators no longer fit in registers beside the flux (tetrahedra N >= 6), or where
-  // the register path's 200-255 registers cap an SM's warps while the tiles would allow
-  // more (triangles N >= 5, tetrahedra N <= 3) -- directly in the shared residual r, which
+  // the register path's 160-255 registers cap an SM's warps while the tiles would allow
+  // more (triangles N >= 3, tetrahedra N <= 3) -- directly in the shared residual r, which
   // this task owns for its line in this phase, with node a's running sum over its pairs in
   // registers (about 96 registers).
-  constexpr bool SACC = D == 3 ? (N >= 6 || N <= 3) : N >= 5;
+  constexpr bool SACC = D == 3 ? (N >= 6 || N <= 3) : N >= 3;
   double acc[N][NC];
   if constexpr (!SACC) {
 #pragma unroll
@@ -1244,9 +1244,9 @@ __device__ __forceinline__ void line_task(int ph, int t, bool act, const DevRef&
                                           const double* __restrict__ fdir, const FluxK& K) {
   constexpr int NC = D + 2;
   // Tetrahedra N >= 6 (N accumulators no longer fit in registers beside the flux), and
-  // triangles N >= 5 and tetrahedra N <= 3 (occupancy): the line's residuals accumulate in
+  // triangles N >= 3 and tetrahedra N <= 3 (occupancy): the line's residuals accumulate in
   // shared memory instead.
-  if constexpr (D == 3 ? (N >= 6 || N <= 3) : N >= 5) {
+  if constexpr (D == 3 ? (N >= 6 || N <= 3) : N >= 3) {
     line_task_shared<D, N, OTF>(ph, t, act, R, M, eg, Sv, Sf, r, h4, vdir, fdir, K);
     return;
   }
