@@ -795,6 +795,58 @@ def run_sweep(args):
                       "l2": "flushed (256 MB write) before every timed call", "dtype": "f64"}), flush=True)
 
 
+def run_partition(args):
+    """The element partition with its facet-trace exchange on one GPU: the benchmark mesh
+    (24576 curved tetrahedra, p = 4, TGV) evaluated whole (esd_rhs) and split into 2 slabs
+    and into 8 round-robin partitions, each partition phase by phase (esd_rhs_begin, trace
+    export / import, esd_rhs_end) on one stream; results checked bitwise against the whole
+    mesh.  One line per split; L2 flushed before every timed call."""
+    import torch
+    import paper_2312_07874_gb300 as E
+    from paper_2312_07874_gb300.partition import split, LocalExchange
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(32 * 1024 * 1024, dtype=torch.float64, device=dev)
+    mesh, gm, u0, dt = build_inputs(torch, E, dev)
+    gm.autotune(u0)
+    X = I.config_mesh(3, WORKLOAD["M"], WORKLOAD["L"], WORKLOAD["p"], True)[1]
+    ref = torch.empty_like(u0)
+    whole_ms = _time_flushed(torch, stream, lambda: E.esd_rhs(gm.handle, u0, ref, stream), args.steps, flush)
+    E.esd_rhs(gm.handle, u0, ref, stream)
+    stream.synchronize()
+    c = X.mean(axis=1)[:, 0]
+    for name, owner in (("2 slabs", (c >= np.median(c)).astype(np.int64)),
+                        ("8 round-robin partitions", np.arange(len(X)) % 8)):
+        parts = split(mesh.nbr_elem, mesh.nbr_face, owner)
+        ms = [E.Mesh(3, WORKLOAD["p"], pt.map_nodes(X), pt.nbr_elem, pt.nbr_face, n_ghost=pt.n_ghost) for pt in parts]
+        loc = [torch.from_numpy(pt.local).to(dev) for pt in parts]
+        us = [u0[i].contiguous() for i in loc]
+        for m, up in zip(ms, us):
+            m.autotune(up, E.ESD_TUNE_PROJECT | E.ESD_TUNE_RESIDUAL)
+        outs = [torch.empty_like(up) for up in us]
+        exchange = LocalExchange(ms, parts, E.ESD_TRACE_STATES)   # index lists and buffers set up once
+
+        def phased():
+            for m, up in zip(ms, us):
+                E.esd_rhs_begin(m.handle, up, stream)
+            exchange(stream)
+            for m, o in zip(ms, outs):
+                E.esd_rhs_end(m.handle, o, stream)
+        with torch.cuda.stream(stream):
+            ms_split = _time_flushed(torch, stream, phased, args.steps, flush)
+            phased()
+        stream.synchronize()
+        exact = all(bool(torch.equal(o, ref[i])) for o, i in zip(outs, loc))
+        _, per_s, _ = E.esd_part_info(ms[0].handle)
+        ghosts = sum(pt.n_ghost for pt in parts)
+        print(json.dumps({"kind": "partition", "workload": f"tet_tgv_curved p={WORKLOAD['p']} ({len(X)} elements), {name}",
+                          "esd_rhs_ms": whole_ms, "phased_ms": ms_split, "overhead": ms_split / whole_ms - 1.0,
+                          "ghost_elements": ghosts, "trace_bytes_per_rhs": ghosts * per_s * 8,
+                          "bitwise_equal_to_whole_mesh": exact,
+                          "l2": "flushed (256 MB write) before every timed call", "dtype": "f64"}), flush=True)
+        del ms
+
+
 def run_skew(args):
     """The skew-symmetric form (esd_rhs_skew, Eq. (rhs_skew)) against the entropy-stable
     esd_rhs on the same meshes and states: 24576 curved tetrahedra (TGV) and 8192 curved
@@ -952,6 +1004,8 @@ def main():
                     "esd_rhs on the tetrahedron and triangle workloads at p = 4")
     ap.add_argument("--sweep", action="store_true", help="per-degree throughput of the triangle and "
                     "tetrahedron workloads and the differentiation workload (one line each)")
+    ap.add_argument("--partition", action="store_true", help="the benchmark mesh split into element "
+                    "partitions with the facet-trace exchange, against the whole mesh (one GPU)")
     args = ap.parse_args()
     WORKLOAD["M"] = args.mesh_m
     if args.batch:
@@ -968,6 +1022,9 @@ def main():
         return
     if args.directions:
         run_directions(args)
+        return
+    if args.partition:
+        run_partition(args)
         return
     if args.warmup < 3:
         args.warmup = 3

@@ -94,20 +94,35 @@ def split(nbr_elem, nbr_face, owner):
     return parts
 
 
+class LocalExchange:
+    """A planned exchange between partition meshes of this process (one GPU): the element
+    lists of every ordered pair (q -> r) and their message buffers are set up once on the
+    device, and each call only launches the export and import kernels (q exports the traces
+    of r's ghosts it owns into a buffer, r imports them into its ghost range).  kind:
+    ESD_TRACE_STATES or ESD_TRACE_COTANGENTS."""
+
+    def __init__(self, meshes, parts, kind):
+        import torch
+        from . import ESD_TRACE_STATES, esd_part_info
+        self.meshes, self.kind, self.plan = meshes, kind, []
+        for r, part in enumerate(parts):
+            for q, (first, n) in part.recv.items():
+                _, per_s, per_c = esd_part_info(meshes[q].handle)
+                per = per_s if kind == ESD_TRACE_STATES else per_c
+                elems = torch.from_numpy(parts[q].send[r]).to("cuda")
+                buf = torch.empty((n, per), dtype=torch.float64, device="cuda")
+                self.plan.append((q, r, elems, buf, first, n))
+
+    def __call__(self, stream=None):
+        from . import esd_part_export, esd_part_import
+        for q, r, elems, buf, first, n in self.plan:
+            esd_part_export(self.meshes[q].handle, self.kind, elems, buf, stream)
+            esd_part_import(self.meshes[r].handle, self.kind, buf, first, n, stream)
+
+
 def exchange_local(meshes, parts, kind, stream=None):
-    """One exchange between partition meshes of this process (one GPU): for every ordered
-    pair (q -> r), q exports the traces of r's ghosts it owns into a device buffer and r
-    imports them into its ghost range.  kind: ESD_TRACE_STATES or ESD_TRACE_COTANGENTS."""
-    import torch
-    from . import ESD_TRACE_STATES, esd_part_export, esd_part_import, esd_part_info
-    for r, part in enumerate(parts):
-        for q, (first, n) in part.recv.items():
-            _, per_s, per_c = esd_part_info(meshes[q].handle)
-            per = per_s if kind == ESD_TRACE_STATES else per_c
-            elems = torch.from_numpy(parts[q].send[r]).to("cuda")
-            buf = torch.empty((n, per), dtype=torch.float64, device="cuda")
-            esd_part_export(meshes[q].handle, kind, elems, buf, stream)
-            esd_part_import(meshes[r].handle, kind, buf, first, n, stream)
+    """One exchange between partition meshes of this process (a LocalExchange used once)."""
+    LocalExchange(meshes, parts, kind)(stream)
 
 
 def exchange_dist(part, export, import_, per, dist, device="cpu", dtype=None):
