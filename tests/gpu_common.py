@@ -63,7 +63,7 @@ def to_dev(a):
 #     on every element computed.  Rounding of a sum of n terms is at most ~n u of this
 #     scale (u = 1.1e-16), while a dropped, mis-signed or mis-indexed term is a sizeable
 #     fraction of it.
-# (3) flat: the benchmark spec's 1e-12 relative max-norm per variable, against the oracle
+# (3) flat: the 1e-12 relative max-norm parity target per variable, against the oracle
 #     evaluated in long double, for every variable where an FP64 evaluation of the method
 #     can meet it: where the FP64 oracle's own error e_64 is below half of it (FLAT_REACH).
 #     The FP64 oracle is not the yardstick itself: at the benchmark size its error on the

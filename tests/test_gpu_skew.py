@@ -3,7 +3,7 @@ skew-symmetric form (oracle/skew.py), for the compressible Euler equations and f
 linear advection, element by element on small curved meshes (several tiles and a ragged
 last tile, every degree class).  Criteria as for the entropy-stable residual
 (gpu_common): accuracy against the oracle in long double within 10 x the FP64 oracle's own
-error, and the benchmark spec's 1e-12 against long double where an FP64 evaluation reaches it."""
+error, and the 1e-12 parity target against long double where an FP64 evaluation reaches it."""
 import numpy as np
 import pytest
 
